@@ -1,0 +1,204 @@
+/*
+ * conreg.h -- C ABI of the GB300 greedy low-rank solver for the spatially
+ * smoothed connectome regression
+ *
+ *   min_W  1/2 || (W X - Y) o Omega ||_F^2 + lambda/2 || L_y W + W L_x^T ||_F^2     (Eq. obj_fun)
+ *
+ * whose normal equations are the multi-term Sylvester equation
+ *
+ *   A(W) := lambda (W L_x^2 + 2 L_y W L_x + L_y^2 W) + sum_a diag(Omega_a) W X_a X_a^T
+ *         = D := (Omega o Y) X^T                                                    (Eq. multitermSylv)
+ *
+ * The solution is grown as W = U Z V^T (U, V orthonormal) by rank-one ALS
+ * updates (Eqs. ALS_linsys, ALS_linsys_v), each followed by a Galerkin
+ * projection (Eq. Proj_Sylv): Algorithm 1 of the paper.
+ *
+ * Conventions for every entry point:
+ *  - Matrices are column-major with an explicit leading dimension (ld >= rows).
+ *  - Pointers named *_host are host memory; the library copies inputs at the
+ *    call and the caller keeps ownership.  Pointers named *_dev are device
+ *    memory of the problem's GPU, read/written on the problem's stream.
+ *  - Every call returns a cr_status; nothing aborts or throws across the ABI.
+ *    On failure cr_last_error() describes the cause.  Device-side loops are
+ *    bounded by iteration caps and report CR_ENOTCONV instead of spinning.
+ *  - A problem object is used by one host thread at a time.
+ */
+#ifndef CONREG_H
+#define CONREG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CR_OK = 0,
+  CR_EINVAL = 1,    /* invalid argument (sizes, NaN/Inf input, non-symmetric Laplacian, ...) */
+  CR_ENOMEM = 2,    /* device allocation failed; nothing leaked */
+  CR_ECUDA = 3,     /* a CUDA runtime call failed */
+  CR_ENOTCONV = 4,  /* an iteration hit its cap; the best iterate is kept */
+  CR_ETIMEOUT = 5,  /* reserved: wall-clock budget exceeded */
+  CR_ERANK = 6,     /* orthogonalisation rejected a new column (rank deficient) */
+  CR_ESTATE = 7     /* call not valid in the current state (e.g. rank capacity reached) */
+} cr_status;
+
+typedef enum { CR_FP64 = 0, CR_MIXED = 1 } cr_precision;
+typedef enum { CR_PRECOND_JACOBI = 0, CR_PRECOND_LEARNED = 1 } cr_precond;
+typedef enum { CR_STOP_NONE = 0, CR_STOP_RMAX = 1, CR_STOP_DW = 2, CR_STOP_RELRES = 3, CR_STOP_RANK = 4 } cr_stop;
+
+/* Square sparse matrix in CSR form (host memory): row i holds entries
+ * rowptr[i] .. rowptr[i+1]-1 with column col[p] and value val[p]. */
+typedef struct {
+  int64_t n;
+  const int32_t* rowptr; /* n + 1 */
+  const int32_t* col;    /* rowptr[n] */
+  const double* val;     /* rowptr[n] */
+} cr_csr;
+
+/* Problem data, Algorithm 1's input line (Sec. 1.1 and Sec. 1.4):
+ *  Lx (nx x nx), Ly (ny x ny): symmetric graph Laplacians of the voxel
+ *      face-adjacency graphs (Sec. 1.1).  Any symmetric CSR matrix is accepted;
+ *      each row may hold at most 16 off-diagonal entries.
+ *  X  (nx x ninj): injection (source) data, column a = injection a.
+ *  Y  (ny x ninj): projection (target) data.
+ *  Omega (ny x ninj): 1 where Y is observed, 0 on the injection site.
+ *  lambda > 0: the weight of Eq. (obj_fun) (not the rescaled lambda-bar; see
+ *      cr_lambda_from_bar).  All pointers are host memory and are copied. */
+typedef struct {
+  int64_t nx, ny, ninj;
+  cr_csr Lx, Ly;
+  const double* X_host;
+  int64_t ldx;
+  const double* Y_host;
+  int64_t ldy;
+  const uint8_t* Omega_host;
+  int64_t ldo;
+  double lambda;
+} cr_problem_desc;
+
+/* Solver options; call cr_options_default() first, then override fields. */
+typedef struct {
+  size_t struct_size;      /* sizeof(cr_options) */
+  int32_t r_cap;           /* rank capacity; device memory is sized for it */
+  int32_t precision;       /* cr_precision */
+  int32_t precond;         /* cr_precond (u/v sub-solves) */
+  double pcg_tol;          /* relative residual of the u/v PCG solves (default 1e-10) */
+  int32_t pcg_maxit;       /* cap on PCG iterations per solve (default 20000) */
+  double als_delta;        /* ALS stop: |‖û‖/‖v̂‖ - 1| <= als_delta (default 0.1, Sec. 2.3) */
+  int32_t als_max_iter;    /* cap on ALS sweeps (default 10) */
+  int32_t als_sweeps;      /* > 0: run exactly this many sweeps (deterministic comparisons) */
+  int32_t galerkin_maxit;  /* cap on Galerkin CG iterations per projection (default 10 j^2 + 100) */
+  int32_t residual_every;  /* cr_solve: evaluate ‖R‖_F every k steps (default 1) */
+  int32_t cluster_size;    /* PCG thread-block cluster size; 0 = automatic */
+  uint64_t seed;           /* seed of the fallback ALS start vector */
+  void* stream;            /* cudaStream_t for all device work; NULL = a library-owned stream */
+  /* Optional device allocator (e.g. a framework caching allocator).  When
+   * alloc is NULL the library uses cudaMalloc/cudaFree. */
+  void* (*alloc)(size_t bytes, void* ctx);
+  void (*free)(void* ptr, size_t bytes, void* ctx);
+  void* alloc_ctx;
+} cr_options;
+
+typedef struct {
+  int32_t rank;          /* rank j after the call */
+  int32_t sweeps;        /* ALS sweeps taken */
+  double delta;          /* final ALS delta */
+  double unorm, vnorm;   /* ‖û‖, ‖v̂‖ of the last sweep */
+  int32_t pcg_iters_u;   /* total PCG iterations, u side */
+  int32_t pcg_iters_v;   /* total PCG iterations, v side */
+  double pcg_relres_max; /* worst final PCG relative residual */
+} cr_rank1_info;
+
+typedef struct {
+  int32_t iters;   /* Galerkin CG iterations */
+  double relres;   /* ‖U^T D V - K(Z)‖_F / ‖U^T D V‖_F at exit */
+} cr_proj_info;
+
+typedef struct {
+  int32_t rank;        /* final rank */
+  int32_t stop;        /* cr_stop */
+  double relres;       /* last evaluated ‖D - A(W)‖_F / ‖D‖_F */
+  double dW;           /* last ‖W_j - W_{j-1}‖_F / ‖W_j‖_F */
+  double J;            /* objective of Eq. (obj_fun) at the final W */
+  int64_t pcg_iters;   /* total PCG iterations */
+  int64_t cg_iters;    /* total Galerkin CG iterations */
+  double seconds;      /* host wall time of the call */
+} cr_solve_info;
+
+/* Fill *o with defaults (struct_size set).  Always succeeds for o != NULL. */
+cr_status cr_options_default(cr_options* o);
+
+/* lambda = lambda_bar * ninj / nx (Sec. 1.1). */
+double cr_lambda_from_bar(double lambda_bar, int64_t ninj, int64_t nx);
+
+/* Create a problem on the current CUDA device: validates and copies the inputs
+ * (Algorithm 1, "Initialize": W_0 = 0, R_0 = D, U_0 = V_0 = []).  Fails with
+ * CR_EINVAL on bad sizes, non-finite values, non-symmetric Laplacians or
+ * lambda <= 0; CR_ENOMEM if device memory for rank r_cap does not fit.
+ * *out is NULL on failure. */
+cr_status cr_create(const cr_problem_desc* desc, const cr_options* opts, struct cr_problem** out);
+
+/* Destroy a problem and free its device memory; NULL is a no-op. */
+void cr_destroy(struct cr_problem* p);
+
+/* One greedy rank-one step (Algorithm 1, body up to "Increment rank"): ALS
+ * sweeps solving Eq. (ALS_linsys) and Eq. (ALS_linsys_v) by PCG until
+ * delta <= als_delta, then orthogonalisation of u and v into U and V (j -> j+1)
+ * and update of the projected coefficient matrices of Eq. (Proj_Sylv).  Z is
+ * padded with a zero row/column (the warm start of the next projection).
+ * CR_ESTATE if j == r_cap, CR_ERANK if u or v lies in the current span. */
+cr_status cr_add_rank_one(struct cr_problem* p, cr_rank1_info* info);
+
+/* Galerkin projection (Eq. Proj_Sylv): matrix CG on Z from the current Z until
+ * ‖U^T D V - K(Z)‖_F <= tol ‖U^T D V‖_F (Algorithm 1 uses tol = tau / 2). */
+cr_status cr_project(struct cr_problem* p, double tol, cr_proj_info* info);
+
+/* Stopping quantities of Algorithm 1 for W = U Z V^T: relres = ‖D - A(W)‖_F/‖D‖_F
+ * (any pointer may be NULL to skip it), J = objective of Eq. (obj_fun), and
+ * dW = ‖W_j - W_{j-1}‖_F / ‖W_j‖_F against the W before the last projection. */
+cr_status cr_residual(struct cr_problem* p, double* relres, double* J, double* dW);
+
+/* Algorithm 1: repeat add_rank_one + project(tau/2) + residual until j == r_max,
+ * dW <= tau, or relres <= relres_target (0 disables that test). */
+cr_status cr_solve(struct cr_problem* p, int32_t r_max, double tau, double relres_target, cr_solve_info* info);
+
+/* Current rank j. */
+cr_status cr_get_rank(const struct cr_problem* p, int32_t* j);
+
+/* Copy U (ny x j), Z (j x j), V (nx x j) into caller host buffers (any may be NULL). */
+cr_status cr_get_factors(struct cr_problem* p, double* U_host, int64_t ldu, double* Z_host, int64_t ldz,
+                         double* V_host, int64_t ldv);
+
+/* Replace the state by rank j factors (U, V must have orthonormal columns; the
+ * library does not re-orthogonalise) and rebuild every projection: checkpoint
+ * restore and step-by-step comparisons. */
+cr_status cr_set_factors(struct cr_problem* p, int32_t j, const double* U_host, int64_t ldu, const double* Z_host,
+                         int64_t ldz, const double* V_host, int64_t ldv);
+
+/* out = R_j v (trans = 0; v has nx entries, out ny) or out = R_j^T u (trans = 1)
+ * for R_j = D - A(U Z V^T): the right sides of Eqs. (ALS_linsys), (ALS_linsys_v). */
+cr_status cr_apply_residual(struct cr_problem* p, int32_t trans, const double* in_host, double* out_host);
+
+/* Solve Eq. (ALS_linsys): A_hat u_hat = rhs for a unit vector v (nx entries),
+ * by the library's PCG to opts.pcg_tol.  rhs and u_hat have ny entries; iters
+ * (may be NULL) receives the PCG iteration count.  CR_ENOTCONV at the cap. */
+cr_status cr_solve_u(struct cr_problem* p, const double* v_host, const double* rhs_host, double* u_hat_host,
+                     int32_t* iters);
+
+/* Solve Eq. (ALS_linsys_v): B_hat v_hat = rhs for a unit vector u (ny entries). */
+cr_status cr_solve_v(struct cr_problem* p, const double* u_host, const double* rhs_host, double* v_hat_host,
+                     int32_t* iters);
+
+/* Static description of a status code. */
+const char* cr_status_str(cr_status s);
+
+/* Message of the last failure on p (or of the last failed cr_create when p is NULL). */
+const char* cr_last_error(const struct cr_problem* p);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CONREG_H */

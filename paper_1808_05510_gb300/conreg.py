@@ -1,0 +1,308 @@
+"""Thin Python binding of the libconreg C ABI (``include/conreg.h``).
+
+Argument marshalling only: every numerical step runs in the CUDA library.  The
+functions keep the C names (``cr_create``, ``cr_add_rank_one``, ...); the
+``ConReg`` class wraps a problem handle.  PyTorch supplies device memory (its
+caching allocator is passed as the library's allocator hook) and the CUDA
+stream.  There is no CPU fallback: without the built library or a GPU every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libconreg.so")
+_lib = None
+
+CR_OK, CR_EINVAL, CR_ENOMEM, CR_ECUDA, CR_ENOTCONV, CR_ETIMEOUT, CR_ERANK, CR_ESTATE = range(8)
+CR_FP64, CR_MIXED = 0, 1
+STOP_NAMES = {0: "none", 1: "r_max", 2: "dW", 3: "relres", 4: "rank"}
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+_up = C.POINTER(C.c_uint8)
+
+
+class cr_csr(C.Structure):
+    _fields_ = [("n", C.c_int64), ("rowptr", _ip), ("col", _ip), ("val", _dp)]
+
+
+class cr_problem_desc(C.Structure):
+    _fields_ = [("nx", C.c_int64), ("ny", C.c_int64), ("ninj", C.c_int64), ("Lx", cr_csr), ("Ly", cr_csr),
+                ("X_host", _dp), ("ldx", C.c_int64), ("Y_host", _dp), ("ldy", C.c_int64),
+                ("Omega_host", _up), ("ldo", C.c_int64), ("lambda_", C.c_double)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
+
+
+class cr_options(C.Structure):
+    _fields_ = [("struct_size", C.c_size_t), ("r_cap", C.c_int32), ("precision", C.c_int32),
+                ("precond", C.c_int32), ("pcg_tol", C.c_double), ("pcg_maxit", C.c_int32),
+                ("als_delta", C.c_double), ("als_max_iter", C.c_int32), ("als_sweeps", C.c_int32),
+                ("galerkin_maxit", C.c_int32), ("residual_every", C.c_int32), ("cluster_size", C.c_int32),
+                ("seed", C.c_uint64), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_ctx", C.c_void_p)]
+
+
+class cr_rank1_info(C.Structure):
+    _fields_ = [("rank", C.c_int32), ("sweeps", C.c_int32), ("delta", C.c_double), ("unorm", C.c_double),
+                ("vnorm", C.c_double), ("pcg_iters_u", C.c_int32), ("pcg_iters_v", C.c_int32),
+                ("pcg_relres_max", C.c_double)]
+
+
+class cr_proj_info(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("relres", C.c_double)]
+
+
+class cr_solve_info(C.Structure):
+    _fields_ = [("rank", C.c_int32), ("stop", C.c_int32), ("relres", C.c_double), ("dW", C.c_double),
+                ("J", C.c_double), ("pcg_iters", C.c_int64), ("cg_iters", C.c_int64), ("seconds", C.c_double)]
+
+
+# Every exported symbol with its (restype, argtypes); include/conreg.h declares the same set.
+SIGNATURES = {
+    "cr_options_default": (C.c_int, [C.POINTER(cr_options)]),
+    "cr_lambda_from_bar": (C.c_double, [C.c_double, C.c_int64, C.c_int64]),
+    "cr_create": (C.c_int, [C.POINTER(cr_problem_desc), C.POINTER(cr_options), C.POINTER(C.c_void_p)]),
+    "cr_destroy": (None, [C.c_void_p]),
+    "cr_add_rank_one": (C.c_int, [C.c_void_p, C.POINTER(cr_rank1_info)]),
+    "cr_project": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(cr_proj_info)]),
+    "cr_residual": (C.c_int, [C.c_void_p, _dp, _dp, _dp]),
+    "cr_solve": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_double, C.POINTER(cr_solve_info)]),
+    "cr_get_rank": (C.c_int, [C.c_void_p, _ip]),
+    "cr_get_factors": (C.c_int, [C.c_void_p, _dp, C.c_int64, _dp, C.c_int64, _dp, C.c_int64]),
+    "cr_set_factors": (C.c_int, [C.c_void_p, C.c_int32, _dp, C.c_int64, _dp, C.c_int64, _dp, C.c_int64]),
+    "cr_apply_residual": (C.c_int, [C.c_void_p, C.c_int32, _dp, _dp]),
+    "cr_solve_u": (C.c_int, [C.c_void_p, _dp, _dp, _dp, _ip]),
+    "cr_solve_v": (C.c_int, [C.c_void_p, _dp, _dp, _dp, _ip]),
+    "cr_status_str": (C.c_char_p, [C.c_int]),
+    "cr_last_error": (C.c_char_p, [C.c_void_p]),
+}
+
+
+class ConRegError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load libconreg.so (built by ``paper_1808_05510_gb300.build``); raises if missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError("libconreg.so is not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = C.CDLL(_LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray, t=_dp):
+    return a.ctypes.data_as(t)
+
+
+def _check(st: int, handle=None, where: str = ""):
+    if st != CR_OK:
+        lib = load()
+        msg = lib.cr_last_error(handle).decode() if lib.cr_last_error(handle) else ""
+        raise ConRegError(st, f"{where}: {lib.cr_status_str(st).decode()}: {msg}")
+
+
+def _f64(a) -> np.ndarray:
+    return np.asfortranarray(np.asarray(a, dtype=np.float64))
+
+
+class _TorchAllocator:
+    """Routes the library's device allocations through torch's caching allocator."""
+
+    def __init__(self, stream_ptr: int):
+        import torch
+
+        self._torch = torch
+        self._stream = stream_ptr
+        self._alloc = ALLOC_FN(self._do_alloc)
+        self._free = FREE_FN(self._do_free)
+
+    def _do_alloc(self, nbytes, ctx):
+        try:
+            return int(self._torch.cuda.caching_allocator_alloc(int(nbytes), stream=self._stream))
+        except Exception:  # out of memory -> the library reports CR_ENOMEM
+            return None
+
+    def _do_free(self, ptr, nbytes, ctx):
+        self._torch.cuda.caching_allocator_delete(ptr)
+
+
+def default_options(**kw) -> cr_options:
+    o = cr_options()
+    _check(load().cr_options_default(C.byref(o)), None, "cr_options_default")
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+class ConReg:
+    """One problem instance on the current CUDA device (see ``include/conreg.h``)."""
+
+    def __init__(self, Lx, Ly, X, Y, Omega, lam: float, stream=None, use_torch_allocator: bool = True, **opts):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("ConReg needs a CUDA device")
+        lib = load()
+        self._lib = lib
+        self._keep = []
+        self.X = _f64(X)
+        self.Y = _f64(Y)
+        self.Om = np.asfortranarray(np.asarray(Omega, dtype=np.uint8))
+        self.nx, self.m = self.X.shape
+        self.ny = self.Y.shape[0]
+        d = cr_problem_desc()
+        d.nx, d.ny, d.ninj = self.nx, self.ny, self.m
+        for name, L in (("Lx", Lx), ("Ly", Ly)):
+            rp = np.ascontiguousarray(L.rowptr, dtype=np.int32)
+            co = np.ascontiguousarray(L.col, dtype=np.int32)
+            va = np.ascontiguousarray(L.val, dtype=np.float64)
+            self._keep += [rp, co, va]
+            setattr(d, name, cr_csr(L.n, _ptr(rp, _ip), _ptr(co, _ip), _ptr(va)))
+        d.X_host, d.ldx = _ptr(self.X), self.nx
+        d.Y_host, d.ldy = _ptr(self.Y), self.ny
+        d.Omega_host, d.ldo = _ptr(self.Om, _up), self.ny
+        d.lambda_ = float(lam)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        o = default_options(**opts)
+        o.stream = C.c_void_p(stream.cuda_stream)
+        self._allocator = None
+        if use_torch_allocator:
+            self._allocator = _TorchAllocator(stream.cuda_stream)
+            o.alloc = self._allocator._alloc
+            o.free = self._allocator._free
+        self.options = o
+        h = C.c_void_p()
+        st = lib.cr_create(C.byref(d), C.byref(o), C.byref(h))
+        _check(st, None, "cr_create")
+        self.h = h
+        self.lam = float(lam)
+
+    @classmethod
+    def from_problem(cls, p, **kw) -> "ConReg":
+        return cls(p.Lx, p.Ly, p.X, p.Y, p.Omega, p.lam, **kw)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.cr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---- Algorithm 1 steps -------------------------------------------------
+    def cr_add_rank_one(self) -> dict:
+        info = cr_rank1_info()
+        st = self._lib.cr_add_rank_one(self.h, C.byref(info))
+        if st not in (CR_OK, CR_ENOTCONV):
+            _check(st, self.h, "cr_add_rank_one")
+        out = {k: getattr(info, k) for k, _ in cr_rank1_info._fields_}
+        out["status"] = st
+        return out
+
+    def cr_project(self, tol: float) -> dict:
+        info = cr_proj_info()
+        st = self._lib.cr_project(self.h, float(tol), C.byref(info))
+        if st not in (CR_OK, CR_ENOTCONV):
+            _check(st, self.h, "cr_project")
+        return {"iters": info.iters, "relres": info.relres, "status": st}
+
+    def cr_residual(self, relres=True, J=True, dW=True):
+        a, b, c = C.c_double(np.nan), C.c_double(np.nan), C.c_double(np.nan)
+        st = self._lib.cr_residual(self.h, C.byref(a) if relres else None, C.byref(b) if J else None,
+                                   C.byref(c) if dW else None)
+        _check(st, self.h, "cr_residual")
+        return {"relres": a.value, "J": b.value, "dW": c.value}
+
+    def cr_solve(self, r_max: int, tau: float, relres_target: float = 0.0) -> dict:
+        info = cr_solve_info()
+        st = self._lib.cr_solve(self.h, int(r_max), float(tau), float(relres_target), C.byref(info))
+        if st not in (CR_OK, CR_ENOTCONV):
+            _check(st, self.h, "cr_solve")
+        out = {k: getattr(info, k) for k, _ in cr_solve_info._fields_}
+        out["stop_name"] = STOP_NAMES.get(info.stop, "?")
+        out["status"] = st
+        return out
+
+    def cr_get_rank(self) -> int:
+        j = C.c_int32()
+        _check(self._lib.cr_get_rank(self.h, C.byref(j)), self.h, "cr_get_rank")
+        return j.value
+
+    def cr_get_factors(self):
+        j = self.cr_get_rank()
+        U = np.zeros((self.ny, j), order="F")
+        Z = np.zeros((j, j), order="F")
+        V = np.zeros((self.nx, j), order="F")
+        if j:
+            _check(self._lib.cr_get_factors(self.h, _ptr(U), self.ny, _ptr(Z), j, _ptr(V), self.nx), self.h,
+                   "cr_get_factors")
+        return U, Z, V
+
+    def cr_set_factors(self, U, Z, V):
+        U, Z, V = _f64(U), _f64(Z), _f64(V)
+        j = Z.shape[0]
+        _check(self._lib.cr_set_factors(self.h, j, _ptr(U), max(1, self.ny), _ptr(Z), max(1, j), _ptr(V),
+                                        max(1, self.nx)), self.h, "cr_set_factors")
+
+    def cr_apply_residual(self, vec, trans: bool = False) -> np.ndarray:
+        vec = np.ascontiguousarray(vec, dtype=np.float64)
+        out = np.zeros(self.nx if trans else self.ny)
+        _check(self._lib.cr_apply_residual(self.h, int(trans), _ptr(vec), _ptr(out)), self.h, "cr_apply_residual")
+        return out
+
+    def cr_solve_u(self, v, rhs):
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+        out = np.zeros(self.ny)
+        it = C.c_int32()
+        st = self._lib.cr_solve_u(self.h, _ptr(v), _ptr(rhs), _ptr(out), C.byref(it))
+        _check(st, self.h, "cr_solve_u")
+        return out, it.value
+
+    def cr_solve_v(self, u, rhs):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+        out = np.zeros(self.nx)
+        it = C.c_int32()
+        st = self._lib.cr_solve_v(self.h, _ptr(u), _ptr(rhs), _ptr(out), C.byref(it))
+        _check(st, self.h, "cr_solve_v")
+        return out, it.value
+
+
+def cr_lambda_from_bar(lam_bar: float, ninj: int, nx: int) -> float:
+    return load().cr_lambda_from_bar(float(lam_bar), int(ninj), int(nx))

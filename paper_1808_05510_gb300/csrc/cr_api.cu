@@ -1,0 +1,1259 @@
+// C ABI of libconreg: problem set-up and the host-side driver of Algorithm 1
+// (greedy rank-1 ALS updates, orthogonalisation, Galerkin projection,
+// residual).  Every numerical step runs in the kernels of cr_pcg.cu,
+// cr_blas.cu and cr_small.cu on the problem's stream; the host only sequences
+// launches and reads back the few scalars that decide control flow (the ALS
+// test, the Galerkin CG test, the stopping test).
+//
+// Residual products without forming R_j (Sec. 2.3, right sides of Eqs.
+// ALS_linsys / ALS_linsys_v).  For W = U Z V^T,
+//   R_j v   = E (X^T v) - lam [U Z (V^T L_x^2 v) + 2 L_yU Z (V^T L_x v) + L_y^2 U Z (V^T v)]
+//   R_j^T u = X (E^T u) - lam [L_x^2 V Z^T (U^T u) + 2 L_xV Z^T (U^T L_y u) + V Z^T (U^T L_y^2 u)]
+// with E = Omega o (Y - U Z V^T X), because D - C(W) = (Omega o (Y - W X)) X^T.
+// With the interleaved panels UU = [u_p, L u_p, L^2 u_p]_p and VV likewise each
+// product is E-times-vector plus one panel-times-vector with a 3j coefficient
+// vector (zcoef).
+//
+// Residual norm (Algorithm 1's residual; relative Frobenius norm).  R is never
+// formed: R = [E | UU] M [X | VV]^T with a block core M (build_core).  With
+// orthonormal bases Q_P of span[E | UU] and Q_Q of span[X | VV] and C_P = Q_P^T
+// [E | UU], C_Q = Q_Q^T [X | VV], ||R||_F = ||C_P M C_Q^T||_F.  The bases of
+// UU, X and VV grow by Gram-Schmidt as columns are appended; only E (m columns)
+// is re-orthogonalised at each evaluation.  Nothing is squared, so the norm is
+// accurate far below the 1e-6 relative level (a Gram-matrix formula would lose
+// half the digits to cancellation).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "conreg.h"
+#include "cr_common.cuh"
+
+using namespace cr;
+
+namespace {
+thread_local std::string g_create_err;
+
+enum {
+  DS_UN2 = 0, DS_VN2 = 1, DS_NB = 2, DS_NA = 3, DS_DW = 4, /*5*/ DS_ZKZ = 6, DS_ZF = 7, DS_RN = 8, DS_V0 = 9,
+  DS_GS = 16, DS_COUNT = 32
+};
+
+struct HostScal {
+  PcgStat stat[2];
+  double ds[DS_COUNT];
+};
+}  // namespace
+
+struct cr_problem {
+  int nx = 0, ny = 0, m = 0, rcap = 0;
+  double lam = 0.0;
+  cr_options opt{};
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  std::string err;
+  int j = 0;
+  std::vector<std::pair<void*, size_t>> allocs;
+  DevLap Lx, Ly;
+  int *xc_ptr = nullptr, *xc_row = nullptr;
+  double* xc_val = nullptr;
+  DevXLocal xl;
+  double* OmY = nullptr;
+  uint8_t* Om = nullptr;
+  double *UU = nullptr, *VV = nullptr, *Z = nullptr, *Zprev = nullptr;
+  double *A1 = nullptr, *A2 = nullptr, *B1 = nullptr, *B2 = nullptr, *H = nullptr, *P = nullptr, *G = nullptr,
+         *F = nullptr, *E = nullptr, *Mzh = nullptr;
+  double *u = nullptr, *v = nullptr, *uhat = nullptr, *vhat = nullptr, *rhs_u = nullptr, *rhs_v = nullptr;
+  double *tmpy = nullptr, *tmpx = nullptr, *xi = nullptr, *eta = nullptr, *svec = nullptr, *hc = nullptr,
+         *gc = nullptr, *coef = nullptr, *cvec = nullptr, *Bnm = nullptr;
+  double *pr = nullptr, *pp = nullptr, *ps = nullptr, *pw = nullptr, *pdinv = nullptr, *pomt = nullptr;
+  PcgStat* stat = nullptr;
+  double* ds = nullptr;
+  HostScal* hs = nullptr;  // pinned
+  double *gR = nullptr, *gP = nullptr, *gQ = nullptr, *gZB2 = nullptr, *gZB1 = nullptr, *gZH = nullptr,
+         *gGw = nullptr;
+  double *QL = nullptr, *CL = nullptr, *QR = nullptr, *CRm = nullptr, *Cx = nullptr, *Cx2 = nullptr, *Ep = nullptr,
+         *CE = nullptr, *CP = nullptr, *Mc = nullptr, *T1 = nullptr, *T2 = nullptr, *gram = nullptr, *tmat = nullptr;
+  int nQL = 0, nQR = 0, nQX = 0;
+  int64_t ldcl = 0, ldcr = 0, ldcx = 0, ldcp = 0, ldm = 0;
+  double* ws = nullptr;
+  size_t ws_elems = 0;
+  double Dnorm = 0.0, OmYn2 = 0.0;
+  bool F_valid = false;
+  double last_dW = NAN;
+};
+
+namespace {
+
+#define CUCHK(p, x)                                                                                   \
+  do {                                                                                                \
+    cudaError_t e_ = (x);                                                                             \
+    if (e_ != cudaSuccess) {                                                                          \
+      (p)->err = std::string(#x) + " failed: " + cudaGetErrorString(e_);                              \
+      return CR_ECUDA;                                                                                \
+    }                                                                                                 \
+  } while (0)
+
+#define TRY(x)                         \
+  do {                                 \
+    cr_status s_ = (x);                \
+    if (s_ != CR_OK) return s_;        \
+  } while (0)
+
+cr_status fail(cr_problem* p, cr_status s, const std::string& msg) {
+  p->err = msg;
+  return s;
+}
+
+template <class T>
+cr_status dalloc(cr_problem* p, T** out, size_t count) {
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  void* ptr = nullptr;
+  if (p->opt.alloc) {
+    ptr = p->opt.alloc(bytes, p->opt.alloc_ctx);
+    if (!ptr) return fail(p, CR_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+  } else {
+    cudaError_t e = cudaMalloc(&ptr, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(p, CR_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+  }
+  p->allocs.push_back({ptr, bytes});
+  *out = static_cast<T*>(ptr);
+  CUCHK(p, cudaMemsetAsync(ptr, 0, bytes, p->st));
+  return CR_OK;
+}
+
+template <class T>
+cr_status upload(cr_problem* p, T** out, const std::vector<T>& h) {
+  TRY(dalloc(p, out, h.size()));
+  if (!h.empty()) CUCHK(p, cudaMemcpyAsync(*out, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, p->st));
+  return CR_OK;
+}
+
+cr_status sync(cr_problem* p) {
+  CUCHK(p, cudaGetLastError());
+  CUCHK(p, cudaStreamSynchronize(p->st));
+  return CR_OK;
+}
+
+// Read device scalars ds[lo..lo+cnt) and both PCG stats into the pinned mirror.
+cr_status readback(cr_problem* p, int lo, int cnt, bool stats) {
+  CUCHK(p, cudaMemcpyAsync(p->hs->ds + lo, p->ds + lo, sizeof(double) * cnt, cudaMemcpyDeviceToHost, p->st));
+  if (stats) CUCHK(p, cudaMemcpyAsync(p->hs->stat, p->stat, sizeof(PcgStat) * 2, cudaMemcpyDeviceToHost, p->st));
+  return sync(p);
+}
+
+// --------------------------------------------------------------------------- set-up helpers
+struct HostCSR {
+  int64_t n;
+  std::vector<int32_t> rp, col;
+  std::vector<double> val;
+};
+
+cr_status check_csr(const cr_csr& c, int64_t n, const char* name, std::string& err) {
+  if (c.n != n || !c.rowptr || !c.col || !c.val) {
+    err = std::string(name) + ": size mismatch or null pointer";
+    return CR_EINVAL;
+  }
+  if (c.rowptr[0] != 0) {
+    err = std::string(name) + ": rowptr[0] != 0";
+    return CR_EINVAL;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    if (c.rowptr[i + 1] < c.rowptr[i]) {
+      err = std::string(name) + ": rowptr not monotone";
+      return CR_EINVAL;
+    }
+    int off = 0;
+    for (int32_t q = c.rowptr[i]; q < c.rowptr[i + 1]; ++q) {
+      if (c.col[q] < 0 || c.col[q] >= n || !std::isfinite(c.val[q])) {
+        err = std::string(name) + ": bad column index or non-finite value in row " + std::to_string(i);
+        return CR_EINVAL;
+      }
+      if (c.col[q] != i && c.val[q] != 0.0) ++off;
+    }
+    if (off > kMaxSlots) {
+      err = std::string(name) + ": more than 16 off-diagonal entries in row " + std::to_string(i);
+      return CR_EINVAL;
+    }
+  }
+  // symmetry: compare the entry list with its transpose
+  std::vector<std::tuple<int32_t, int32_t, double>> a, b;
+  const int64_t nnz = c.rowptr[n];
+  a.reserve(nnz);
+  b.reserve(nnz);
+  for (int64_t i = 0; i < n; ++i)
+    for (int32_t q = c.rowptr[i]; q < c.rowptr[i + 1]; ++q)
+      if (c.val[q] != 0.0) {
+        a.emplace_back((int32_t)i, c.col[q], c.val[q]);
+        b.emplace_back(c.col[q], (int32_t)i, c.val[q]);
+      }
+  std::sort(a.begin(), a.end());
+  std::sort(b.begin(), b.end());
+  if (a != b) {
+    err = std::string(name) + ": matrix is not symmetric";
+    return CR_EINVAL;
+  }
+  return CR_OK;
+}
+
+// Build the padded ELL layout and the PCG partition of one Laplacian.
+cr_status build_lap(cr_problem* p, const cr_csr& c, DevLap& L) {
+  const int n = (int)c.n;
+  std::vector<double> diag(n, 0.0), l2(n, 0.0);
+  std::vector<std::vector<std::pair<int, double>>> rows(n);
+  bool unit = true;
+  int K = 1;
+  for (int i = 0; i < n; ++i) {
+    for (int32_t q = c.rowptr[i]; q < c.rowptr[i + 1]; ++q) {
+      const int jj = c.col[q];
+      const double v = c.val[q];
+      if (jj == i) {
+        diag[i] += v;
+      } else if (v != 0.0) {
+        rows[i].push_back({jj, v});
+        if (v != -1.0) unit = false;
+      }
+    }
+    // merge duplicate columns
+    std::sort(rows[i].begin(), rows[i].end());
+    std::vector<std::pair<int, double>> merged;
+    for (auto& e : rows[i]) {
+      if (!merged.empty() && merged.back().first == e.first)
+        merged.back().second += e.second;
+      else
+        merged.push_back(e);
+    }
+    rows[i] = merged;
+    for (auto& e : rows[i])
+      if (e.second != -1.0) unit = false;
+    K = std::max<int>(K, (int)rows[i].size());
+  }
+  for (int i = 0; i < n; ++i) {
+    double s = diag[i] * diag[i];
+    for (auto& e : rows[i]) s += e.second * e.second;
+    l2[i] = s;
+  }
+  // partition for the cluster PCG
+  const size_t smem_cap = 227 * 1024;
+  int desired = std::min(kMaxCluster, std::max(1, (n + 479) / 480));
+  int cs = 0, chunk = 0;
+  for (int c2 = desired; c2 >= 1; --c2) {
+    const int ch = (n + c2 - 1) / c2;
+    const size_t smem = pcg_smem_bytes(ch, p->m);
+    if (smem > smem_cap) break;
+    if (pcg_cluster_ok(c2, smem)) {
+      cs = c2;
+      chunk = ch;
+      break;
+    }
+  }
+  if (cs == 0)
+    return fail(p, CR_EINVAL, "grid of " + std::to_string(n) +
+                                  " voxels does not fit the cluster-resident PCG (shared memory / cluster size)");
+  if (p->opt.cluster_size > 0 && p->opt.cluster_size < cs) {
+    const int c2 = p->opt.cluster_size;
+    const int ch = (n + c2 - 1) / c2;
+    if (pcg_smem_bytes(ch, p->m) <= smem_cap && pcg_cluster_ok(c2, pcg_smem_bytes(ch, p->m))) {
+      cs = c2;
+      chunk = ch;
+    }
+  }
+  std::vector<int> nbr((size_t)K * n, -1), nbrp((size_t)K * n, -1);
+  std::vector<double> offw(unit ? 0 : (size_t)K * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (size_t k = 0; k < rows[i].size(); ++k) {
+      const int jj = rows[i][k].first;
+      nbr[k * n + i] = jj;
+      nbrp[k * n + i] = ((jj / chunk) << 24) | (jj % chunk);
+      if (!unit) offw[k * n + i] = rows[i][k].second;
+    }
+  int *dn = nullptr, *dnp = nullptr;
+  double *dd = nullptr, *dl2 = nullptr, *dw = nullptr;
+  TRY(upload(p, &dn, nbr));
+  TRY(upload(p, &dnp, nbrp));
+  TRY(upload(p, &dd, diag));
+  TRY(upload(p, &dl2, l2));
+  if (!unit) TRY(upload(p, &dw, offw));
+  L.n = n;
+  L.K = K;
+  L.nbr = dn;
+  L.nbrp = dnp;
+  L.offw = dw;
+  L.diag = dd;
+  L.l2diag = dl2;
+  L.chunk = chunk;
+  L.csize = cs;
+  CUCHK(p, pcg_prepare(0, cs, pcg_smem_bytes(chunk, p->m)));
+  return CR_OK;
+}
+
+// Host Jacobi eigen-decomposition of a symmetric n x n matrix (column-major);
+// eigenvectors in V (columns), eigenvalues in w.
+void sym_eig(int n, std::vector<double> A, std::vector<double>& w, std::vector<double>& V) {
+  V.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) V[i + (size_t)i * n] = 1.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int a = 0; a < n; ++a)
+      for (int b = 0; b < n; ++b) {
+        const double x = A[a + (size_t)b * n];
+        tot += x * x;
+        if (a != b) off += x * x;
+      }
+    if (off <= 1e-32 * tot || off == 0.0) break;
+    for (int pp = 0; pp < n - 1; ++pp)
+      for (int qq = pp + 1; qq < n; ++qq) {
+        const double apq = A[pp + (size_t)qq * n];
+        if (apq == 0.0) continue;
+        const double app = A[pp + (size_t)pp * n], aqq = A[qq + (size_t)qq * n];
+        const double th = (aqq - app) / (2.0 * apq);
+        const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+        const double cth = 1.0 / std::sqrt(t * t + 1.0), sth = t * cth;
+        for (int k = 0; k < n; ++k) {
+          const double akp = A[k + (size_t)pp * n], akq = A[k + (size_t)qq * n];
+          A[k + (size_t)pp * n] = cth * akp - sth * akq;
+          A[k + (size_t)qq * n] = sth * akp + cth * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double apk = A[pp + (size_t)k * n], aqk = A[qq + (size_t)k * n];
+          A[pp + (size_t)k * n] = cth * apk - sth * aqk;
+          A[qq + (size_t)k * n] = sth * apk + cth * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double vkp = V[k + (size_t)pp * n], vkq = V[k + (size_t)qq * n];
+          V[k + (size_t)pp * n] = cth * vkp - sth * vkq;
+          V[k + (size_t)qq * n] = sth * vkp + cth * vkq;
+        }
+      }
+  }
+  w.resize(n);
+  for (int i = 0; i < n; ++i) w[i] = A[i + (size_t)i * n];
+}
+
+// --------------------------------------------------------------------------- device steps
+// Gram-Schmidt twice: w <- w - Q (Q^T w) (x2) against Q's first nq columns,
+// then w <- w / |w|.  Returns |w_after| / |w_before| (0 if w was zero).
+cr_status cgs2(cr_problem* p, int n, const double* Q, int64_t ldq, int nq, double* w, double* ratio) {
+  cudaStream_t st = p->st;
+  dot(n, w, w, p->ds + DS_NB, st);
+  for (int pass = 0; pass < 2 && nq > 0; ++pass) {
+    gemv_t(n, nq, Q, ldq, w, p->cvec, 1, 1.0, 0.0, st);
+    gemv_n(n, nq, Q, ldq, p->cvec, 1, w, -1.0, 1.0, st);
+  }
+  dot(n, w, w, p->ds + DS_NA, st);
+  TRY(readback(p, DS_NB, 2, false));
+  const double nb = p->hs->ds[DS_NB], na = p->hs->ds[DS_NA];
+  *ratio = nb > 0.0 ? std::sqrt(na / nb) : 0.0;
+  if (na > 0.0) scale_by_inv_norm(n, w, p->ds + DS_NA, w, st);
+  return CR_OK;
+}
+
+// R_j v (ny entries) for v on the x grid.
+void residual_times(cr_problem* p, const double* vv, double* out) {
+  cudaStream_t st = p->st;
+  const int j = p->j;
+  spmv_xt(p->m, p->xc_ptr, p->xc_row, p->xc_val, vv, p->xi, 1, st);
+  gemv_n(p->ny, p->m, p->E, p->ny, p->xi, 1, out, 1.0, 0.0, st);
+  if (j > 0) {
+    gemv_t(p->nx, 3 * j, p->VV, p->nx, vv, p->hc, 1, 1.0, 0.0, st);
+    zcoef(j, p->Z, p->rcap, 0, p->hc, p->lam, p->gc, st);
+    gemv_n(p->ny, 3 * j, p->UU, p->ny, p->gc, 1, out, -1.0, 1.0, st);
+  }
+}
+
+// R_j^T u (nx entries) for u on the y grid.
+void residual_t_times(cr_problem* p, const double* uu, double* out) {
+  cudaStream_t st = p->st;
+  const int j = p->j;
+  gemv_t(p->ny, p->m, p->E, p->ny, uu, p->eta, 1, 1.0, 0.0, st);
+  spmv_x(p->nx, p->xl.xr_ptr, p->xl.xr_col, p->xl.xr_val, p->eta, out, 1.0, 0.0, st);
+  if (j > 0) {
+    gemv_t(p->ny, 3 * j, p->UU, p->ny, uu, p->hc, 1, 1.0, 0.0, st);
+    zcoef(j, p->Z, p->rcap, 1, p->hc, p->lam, p->gc, st);
+    gemv_n(p->nx, 3 * j, p->VV, p->nx, p->gc, 1, out, -1.0, 1.0, st);
+  }
+}
+
+// u side (Eq. ALS_linsys): coefficients c = v'L_x v, d = |L_x v|^2 and xi = X^T v.
+void prep_u(cr_problem* p, const double* vv) {
+  cudaStream_t st = p->st;
+  lap_apply(p->Lx, vv, p->tmpx, 0.0, st);
+  dot(p->nx, vv, p->tmpx, p->coef + 0, st);
+  dot(p->nx, p->tmpx, p->tmpx, p->coef + 1, st);
+  spmv_xt(p->m, p->xc_ptr, p->xc_row, p->xc_val, vv, p->xi, 1, st);
+}
+
+// v side (Eq. ALS_linsys_v): c' = u'L_y u, d' = |L_y u|^2, s_a = u' diag(Omega_a) u.
+void prep_v(cr_problem* p, const double* uu) {
+  cudaStream_t st = p->st;
+  lap_apply(p->Ly, uu, p->tmpy, 0.0, st);
+  dot(p->ny, uu, p->tmpy, p->coef + 2, st);
+  dot(p->ny, p->tmpy, p->tmpy, p->coef + 3, st);
+  omega_sq_dots(p->ny, p->m, p->Om, p->ny, uu, p->svec, st);
+}
+
+cr_status launch_pcg(cr_problem* p, int side, const double* b, double* x) {
+  PcgArgs a{};
+  a.lam = p->lam;
+  a.m = p->m;
+  a.b = b;
+  a.x = x;
+  a.r = p->pr;
+  a.p = p->pp;
+  a.sv = p->ps;
+  a.w = p->pw;
+  a.dinv = p->pdinv;
+  a.omt = p->pomt;
+  a.tol = p->opt.pcg_tol;
+  a.maxit = p->opt.pcg_maxit;
+  a.stat = p->stat + side;
+  if (side == 0) {
+    a.L = p->Ly;
+    a.coef = p->coef + 0;
+    a.Om = p->Om;
+    a.ldo = p->ny;
+    a.xi = p->xi;
+  } else {
+    a.L = p->Lx;
+    a.coef = p->coef + 2;
+    a.X = p->xl;
+    a.s = p->svec;
+  }
+  CUCHK(p, pcg_launch(a, side, p->st));
+  return CR_OK;
+}
+
+// K(Zin) of Eq. (Proj_Sylv) into Kout (j x j, ld rcap):
+//   lam (Z B2 + 2 A1 Z B1 + A2 Z) + sum_a G_a Z h_a h_a^T,  with the data term
+//   evaluated as [G_1 (Z h_1), ..., G_m (Z h_m)] H^T since each V^T X_a X_a^T V
+//   is the rank-one h_a h_a^T (h_a = V^T X_a).
+void galerkin_apply(cr_problem* p, const double* Zin, double* Kout) {
+  cudaStream_t st = p->st;
+  const int j = p->j, m = p->m;
+  const int64_t ld = p->rcap;
+  MatView Zv{Zin, 1, ld};
+  gemm(j, j, j, 1.0, Zv, MatView{p->B2, 1, ld}, 0.0, p->gZB2, 1, ld, p->ws, p->ws_elems, st);
+  gemm(j, j, j, 1.0, Zv, MatView{p->B1, 1, ld}, 0.0, p->gZB1, 1, ld, p->ws, p->ws_elems, st);
+  gemm(j, m, j, 1.0, Zv, MatView{p->H, 1, ld}, 0.0, p->gZH, 1, ld, p->ws, p->ws_elems, st);
+  mat_axpby(j, j, p->lam, p->gZB2, ld, 0.0, p->gZB2, ld, Kout, ld, st);
+  gemm(j, j, j, 2.0 * p->lam, MatView{p->A1, 1, ld}, MatView{p->gZB1, 1, ld}, 1.0, Kout, 1, ld, p->ws,
+       p->ws_elems, st);
+  gemm(j, j, j, p->lam, MatView{p->A2, 1, ld}, Zv, 1.0, Kout, 1, ld, p->ws, p->ws_elems, st);
+  batched_gemv(j, m, p->G, ld, ld * ld, p->gZH, ld, p->gGw, ld, st);
+  gemm(j, j, m, 1.0, MatView{p->gGw, 1, ld}, MatView{p->H, ld, 1}, 1.0, Kout, 1, ld, p->ws, p->ws_elems, st);
+}
+
+// F = U^T D V = (U^T (Omega o Y)) (X^T V) = P H^T
+void build_F(cr_problem* p) {
+  const int64_t ld = p->rcap;
+  gemm(p->j, p->j, p->m, 1.0, MatView{p->P, 1, ld}, MatView{p->H, ld, 1}, 0.0, p->F, 1, ld, p->ws, p->ws_elems,
+       p->st);
+  p->F_valid = true;
+}
+
+// E = Omega o (Y - U Z H) after Z changed.
+void refresh_E(cr_problem* p) {
+  cudaStream_t st = p->st;
+  const int j = p->j, m = p->m;
+  const int64_t ld = p->rcap;
+  if (j == 0) {
+    copy(p->ny * m, p->OmY, p->E, st);
+    return;
+  }
+  gemm(j, m, j, 1.0, MatView{p->Z, 1, ld}, MatView{p->H, 1, ld}, 0.0, p->Mzh, 1, ld, p->ws, p->ws_elems, st);
+  gemm(p->ny, m, j, 1.0, MatView{p->UU, 1, 3 * (int64_t)p->ny}, MatView{p->Mzh, 1, ld}, 0.0, p->E, 1, p->ny, p->ws,
+       p->ws_elems, st);
+  mask_residual(p->ny, m, p->OmY, p->Om, p->ny, p->E, st);
+}
+
+// Append UU/VV columns 3q..3q+2 to the residual-norm bases.
+cr_status grow_bases(cr_problem* p, int q) {
+  cudaStream_t st = p->st;
+  for (int s = 0; s < 3; ++s) {
+    const double* col = p->UU + (size_t)(3 * q + s) * p->ny;
+    double* dst = p->QL + (size_t)p->nQL * p->ny;
+    copy(p->ny, col, dst, st);
+    double ratio = 0.0;
+    TRY(cgs2(p, p->ny, p->QL, p->ny, p->nQL, dst, &ratio));
+    if (ratio > 1e-12) ++p->nQL;
+  }
+  for (int s = 0; s < 3; ++s)
+    gemv_t(p->ny, p->nQL, p->QL, p->ny, p->UU + (size_t)(3 * q + s) * p->ny, p->CL + (size_t)(3 * q + s) * p->ldcl,
+           1, 1.0, 0.0, st);
+  for (int s = 0; s < 3; ++s) {
+    const double* col = p->VV + (size_t)(3 * q + s) * p->nx;
+    double* dst = p->QR + (size_t)p->nQR * p->nx;
+    copy(p->nx, col, dst, st);
+    double ratio = 0.0;
+    TRY(cgs2(p, p->nx, p->QR, p->nx, p->nQR, dst, &ratio));
+    if (ratio > 1e-12) ++p->nQR;
+  }
+  for (int s = 0; s < 3; ++s)
+    gemv_t(p->nx, p->nQR, p->QR, p->nx, p->VV + (size_t)(3 * q + s) * p->nx,
+           p->CRm + (size_t)(p->m + 3 * q + s) * p->ldcr, 1, 1.0, 0.0, st);
+  return CR_OK;
+}
+
+// Projections for the new column q (u_q, v_q already in UU/VV column 3q):
+// L^s images, borders of U^T L_y^s U, V^T L_x^s V, G_a = U^T diag(Omega_a) U,
+// H = V^T X, P = U^T (Omega o Y), and the residual-norm bases.
+cr_status grow_projections(cr_problem* p, int q) {
+  cudaStream_t st = p->st;
+  const int ny = p->ny, nx = p->nx, m = p->m;
+  const int64_t ld = p->rcap;
+  double* uq = p->UU + (size_t)3 * q * ny;
+  double* vq = p->VV + (size_t)3 * q * nx;
+  lap_apply(p->Ly, uq, uq + ny, 0.0, st);
+  lap_apply(p->Ly, uq + ny, uq + 2 * ny, 0.0, st);
+  lap_apply(p->Lx, vq, vq + nx, 0.0, st);
+  lap_apply(p->Lx, vq + nx, vq + 2 * nx, 0.0, st);
+  const int64_t ldu = 3 * (int64_t)ny, ldv = 3 * (int64_t)nx;
+  gemv_t(ny, q + 1, p->UU, ldu, uq + ny, p->A1 + q * ld, 1, 1.0, 0.0, st);
+  gemv_t(ny, q + 1, p->UU, ldu, uq + 2 * ny, p->A2 + q * ld, 1, 1.0, 0.0, st);
+  gemv_t(nx, q + 1, p->VV, ldv, vq + nx, p->B1 + q * ld, 1, 1.0, 0.0, st);
+  gemv_t(nx, q + 1, p->VV, ldv, vq + 2 * nx, p->B2 + q * ld, 1, 1.0, 0.0, st);
+  mirror_col(q, p->A1, ld, 1, 0, st);
+  mirror_col(q, p->A2, ld, 1, 0, st);
+  mirror_col(q, p->B1, ld, 1, 0, st);
+  mirror_col(q, p->B2, ld, 1, 0, st);
+  spmv_xt(m, p->xc_ptr, p->xc_row, p->xc_val, vq, p->H + q, ld, st);
+  gemv_t(ny, m, p->OmY, ny, uq, p->P + q, ld, 1.0, 0.0, st);
+  omega_times(ny, m, p->Om, ny, uq, p->Bnm, st);
+  gemm(q + 1, m, ny, 1.0, MatView{p->UU, ldu, 1}, MatView{p->Bnm, 1, ny}, 0.0, p->G + q * ld, 1, ld * ld, p->ws,
+       p->ws_elems, st);
+  mirror_col(q, p->G, ld, m, ld * ld, st);
+  return grow_bases(p, q);
+}
+
+cr_status do_project(cr_problem* p, double tol, cr_proj_info* info) {
+  cudaStream_t st = p->st;
+  const int j = p->j;
+  const int64_t ld = p->rcap;
+  if (info) *info = cr_proj_info{0, 0.0};
+  if (j == 0) return CR_OK;
+  CUCHK(p, cudaMemcpyAsync(p->Zprev, p->Z, sizeof(double) * ld * ld, cudaMemcpyDeviceToDevice, st));
+  build_F(p);
+  double* gs = p->ds + DS_GS;
+  galerkin_apply(p, p->Z, p->gQ);
+  mat_axpby(j, j, 1.0, p->F, ld, -1.0, p->gQ, ld, p->gR, ld, st);  // R = F - K(Z)
+  copy2d(j, j, p->gR, ld, p->gP, ld, st);
+  mat_dot(j, j, p->gR, ld, p->gR, ld, gs + 0, st);
+  mat_dot(j, j, p->F, ld, p->F, ld, gs + 3, st);
+  TRY(readback(p, DS_GS, 4, false));
+  const double fn2 = p->hs->ds[DS_GS + 3];
+  double rho = p->hs->ds[DS_GS + 0];
+  const double thr2 = tol * tol * fn2;
+  const int maxit = p->opt.galerkin_maxit > 0 ? p->opt.galerkin_maxit : 10 * j * j + 100;
+  int k = 0;
+  cr_status rc = CR_OK;
+  if (fn2 > 0.0 && rho > thr2) {
+    for (;;) {
+      galerkin_apply(p, p->gP, p->gQ);
+      mat_dot(j, j, p->gP, ld, p->gQ, ld, gs + 2, st);
+      cg_update_zr(j, p->Z, p->gR, p->gP, p->gQ, ld, gs, k, st);
+      mat_dot(j, j, p->gR, ld, p->gR, ld, gs + ((k + 1) & 1), st);
+      cg_update_p(j, p->gP, p->gR, ld, gs, k, st);
+      ++k;
+      const bool check = k < 8 || (k % 4) == 0 || k >= maxit;
+      if (check) {
+        TRY(readback(p, DS_GS, 3, false));
+        rho = p->hs->ds[DS_GS + (k & 1)];
+        if (!(rho > thr2)) break;
+        if (!std::isfinite(rho)) {
+          rc = fail(p, CR_ENOTCONV, "Galerkin CG produced a non-finite residual");
+          break;
+        }
+      }
+      if (k >= maxit) {
+        rc = fail(p, CR_ENOTCONV, "Galerkin CG reached its iteration cap");
+        break;
+      }
+    }
+  }
+  refresh_E(p);
+  TRY(sync(p));
+  if (info) {
+    info->iters = k;
+    info->relres = fn2 > 0.0 ? std::sqrt(std::max(rho, 0.0) / fn2) : 0.0;
+  }
+  return rc;
+}
+
+cr_status do_relres(cr_problem* p, double* relres) {
+  cudaStream_t st = p->st;
+  const int j = p->j, m = p->m, ny = p->ny;
+  const int k = p->nQL;
+  const int64_t ldcx = p->ldcx;
+  // E_perp = E - Q_L (Q_L^T E), twice; Cx accumulates Q_L^T E.
+  copy(ny * m, p->E, p->Ep, st);
+  if (k > 0) {
+    gemm(k, m, ny, 1.0, MatView{p->QL, ny, 1}, MatView{p->E, 1, ny}, 0.0, p->Cx, 1, ldcx, p->ws, p->ws_elems, st);
+    gemm(ny, m, k, -1.0, MatView{p->QL, 1, ny}, MatView{p->Cx, 1, ldcx}, 1.0, p->Ep, 1, ny, p->ws, p->ws_elems, st);
+    gemm(k, m, ny, 1.0, MatView{p->QL, ny, 1}, MatView{p->Ep, 1, ny}, 0.0, p->Cx2, 1, ldcx, p->ws, p->ws_elems, st);
+    gemm(ny, m, k, -1.0, MatView{p->QL, 1, ny}, MatView{p->Cx2, 1, ldcx}, 1.0, p->Ep, 1, ny, p->ws, p->ws_elems, st);
+    mat_axpby(k, m, 1.0, p->Cx2, ldcx, 1.0, p->Cx, ldcx, p->Cx, ldcx, st);
+  }
+  // Q_E: orthonormal basis of span(E_perp) from the eigen-decomposition of its
+  // Gram matrix (host, m x m), applied twice for orthogonality.
+  double* QE = p->QL + (size_t)k * ny;
+  gemm(m, m, ny, 1.0, MatView{p->Ep, ny, 1}, MatView{p->Ep, 1, ny}, 0.0, p->gram, 1, m, p->ws, p->ws_elems, st);
+  std::vector<double> gram((size_t)m * m);
+  CUCHK(p, cudaMemcpyAsync(gram.data(), p->gram, sizeof(double) * m * m, cudaMemcpyDeviceToHost, st));
+  TRY(sync(p));
+  std::vector<double> w, V;
+  sym_eig(m, gram, w, V);
+  double wmax = 0.0;
+  for (double x : w) wmax = std::max(wmax, x);
+  std::vector<double> T;
+  int ke = 0;
+  const double thr = 1e-26 * std::max(wmax, p->Dnorm * p->Dnorm * 1e-30);
+  for (int i = 0; i < m; ++i)
+    if (w[i] > thr && w[i] > 1e-20 * wmax) {
+      for (int r = 0; r < m; ++r) T.push_back(V[r + (size_t)i * m] / std::sqrt(w[i]));
+      ++ke;
+    }
+  if (ke > 0) {
+    CUCHK(p, cudaMemcpyAsync(p->tmat, T.data(), sizeof(double) * T.size(), cudaMemcpyHostToDevice, st));
+    gemm(ny, ke, m, 1.0, MatView{p->Ep, 1, ny}, MatView{p->tmat, 1, m}, 0.0, QE, 1, ny, p->ws, p->ws_elems, st);
+    // second pass: Cholesky of Q_E^T Q_E
+    gemm(ke, ke, ny, 1.0, MatView{QE, ny, 1}, MatView{QE, 1, ny}, 0.0, p->gram, 1, ke, p->ws, p->ws_elems, st);
+    std::vector<double> g2((size_t)ke * ke);
+    CUCHK(p, cudaMemcpyAsync(g2.data(), p->gram, sizeof(double) * ke * ke, cudaMemcpyDeviceToHost, st));
+    TRY(sync(p));
+    // upper Cholesky factor R (g2 = R^T R), then Rinv
+    std::vector<double> R((size_t)ke * ke, 0.0), Ri((size_t)ke * ke, 0.0);
+    bool ok = true;
+    for (int c = 0; c < ke && ok; ++c) {
+      for (int r = 0; r <= c; ++r) {
+        double s = g2[r + (size_t)c * ke];
+        for (int t = 0; t < r; ++t) s -= R[t + (size_t)r * ke] * R[t + (size_t)c * ke];
+        if (r == c) {
+          if (s <= 0.0) {
+            ok = false;
+            break;
+          }
+          R[r + (size_t)c * ke] = std::sqrt(s);
+        } else {
+          R[r + (size_t)c * ke] = s / R[r + (size_t)r * ke];
+        }
+      }
+    }
+    if (ok) {
+      for (int c = 0; c < ke; ++c) {
+        Ri[c + (size_t)c * ke] = 1.0 / R[c + (size_t)c * ke];
+        for (int r = c - 1; r >= 0; --r) {
+          double s = 0.0;
+          for (int t = r + 1; t <= c; ++t) s += R[r + (size_t)t * ke] * Ri[t + (size_t)c * ke];
+          Ri[r + (size_t)c * ke] = -s / R[r + (size_t)r * ke];
+        }
+      }
+      CUCHK(p, cudaMemcpyAsync(p->tmat, Ri.data(), sizeof(double) * Ri.size(), cudaMemcpyHostToDevice, st));
+      copy(ny * ke, QE, p->Bnm, st);
+      gemm(ny, ke, ke, 1.0, MatView{p->Bnm, 1, ny}, MatView{p->tmat, 1, ke}, 0.0, QE, 1, ny, p->ws, p->ws_elems,
+           st);
+    }
+    gemm(ke, m, ny, 1.0, MatView{QE, ny, 1}, MatView{p->Ep, 1, ny}, 0.0, p->CE, 1, m, p->ws, p->ws_elems, st);
+  }
+  // C_P = [[Cx, CL], [CE, 0]]  ((k + ke) x (m + 3j))
+  const int nc = m + 3 * j, kr = k + ke;
+  const int64_t ldcp = p->ldcp;
+  fill((int64_t)ldcp * nc, 0.0, p->CP, st);
+  if (k > 0) {
+    copy2d(k, m, p->Cx, ldcx, p->CP, ldcp, st);
+    copy2d(k, 3 * j, p->CL, p->ldcl, p->CP + (size_t)m * ldcp, ldcp, st);
+  }
+  if (ke > 0) copy2d(ke, m, p->CE, m, p->CP + k, ldcp, st);
+  build_core(m, j, p->Z, p->rcap, p->lam, p->Mc, p->ldm, st);
+  gemm(kr, nc, nc, 1.0, MatView{p->CP, 1, ldcp}, MatView{p->Mc, 1, p->ldm}, 0.0, p->T1, 1, ldcp, p->ws, p->ws_elems,
+       st);
+  gemm(kr, p->nQR, nc, 1.0, MatView{p->T1, 1, ldcp}, MatView{p->CRm, p->ldcr, 1}, 0.0, p->T2, 1, ldcp, p->ws,
+       p->ws_elems, st);
+  mat_dot(kr, p->nQR, p->T2, ldcp, p->T2, ldcp, p->ds + DS_RN, st);
+  TRY(readback(p, DS_RN, 1, false));
+  *relres = p->Dnorm > 0.0 ? std::sqrt(p->hs->ds[DS_RN]) / p->Dnorm : 0.0;
+  return CR_OK;
+}
+
+cr_status do_rank_one(cr_problem* p, cr_rank1_info* info) {
+  cudaStream_t st = p->st;
+  const int ny = p->ny, nx = p->nx, j = p->j;
+  if (j >= p->rcap) return fail(p, CR_ESTATE, "rank capacity r_cap reached");
+  // ALS start vector: v0 = R_j^T 1 / |R_j^T 1|
+  fill(ny, 1.0, p->tmpy, st);
+  residual_t_times(p, p->tmpy, p->v);
+  dot(nx, p->v, p->v, p->ds + DS_V0, st);
+  TRY(readback(p, DS_V0, 1, false));
+  const double v0n2 = p->hs->ds[DS_V0];
+  if (v0n2 > 1e-300 * p->Dnorm * p->Dnorm && std::isfinite(v0n2)) {
+    scale_by_inv_norm(nx, p->v, p->ds + DS_V0, p->v, st);
+  } else {
+    // splitmix64 -> Box-Muller Gaussian, seeded by (seed + j)
+    std::vector<double> g(nx);
+    uint64_t state = p->opt.seed + (uint64_t)j;
+    auto next = [&state]() {
+      uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      return z ^ (z >> 31);
+    };
+    double nrm = 0.0;
+    for (int i = 0; i < nx; ++i) {
+      const double u1 = ((next() >> 11) + 1.0) * (1.0 / 9007199254740993.0);
+      const double u2 = (next() >> 11) * (1.0 / 9007199254740992.0);
+      g[i] = std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+      nrm += g[i] * g[i];
+    }
+    for (double& x : g) x /= std::sqrt(nrm);
+    CUCHK(p, cudaMemcpyAsync(p->v, g.data(), sizeof(double) * nx, cudaMemcpyHostToDevice, st));
+  }
+  fill(ny, 0.0, p->uhat, st);
+  fill(nx, 0.0, p->vhat, st);
+  int sweeps = 0;
+  double delta = INFINITY, un = 0.0, vn = 0.0, worst = 0.0;
+  int itu = 0, itv = 0;
+  for (;;) {
+    prep_u(p, p->v);
+    residual_times(p, p->v, p->rhs_u);
+    TRY(launch_pcg(p, 0, p->rhs_u, p->uhat));
+    dot(ny, p->uhat, p->uhat, p->ds + DS_UN2, st);
+    scale_by_inv_norm(ny, p->uhat, p->ds + DS_UN2, p->u, st);
+    prep_v(p, p->u);
+    residual_t_times(p, p->u, p->rhs_v);
+    TRY(launch_pcg(p, 1, p->rhs_v, p->vhat));
+    dot(nx, p->vhat, p->vhat, p->ds + DS_VN2, st);
+    scale_by_inv_norm(nx, p->vhat, p->ds + DS_VN2, p->v, st);
+    TRY(readback(p, 0, 2, true));
+    const PcgStat* s = p->hs->stat;
+    itu += s[0].iters;
+    itv += s[1].iters;
+    worst = std::max(worst, std::max(s[0].relres, s[1].relres));
+    un = std::sqrt(p->hs->ds[DS_UN2]);
+    vn = std::sqrt(p->hs->ds[DS_VN2]);
+    ++sweeps;
+    if (s[0].status == 2 || s[1].status == 2 || !(un > 0.0) || !(vn > 0.0) || !std::isfinite(un) ||
+        !std::isfinite(vn))
+      return fail(p, CR_ENOTCONV, "ALS sub-solve broke down (indefinite operator or zero solution)");
+    delta = std::fabs(un / vn - 1.0);
+    if (p->opt.als_sweeps > 0) {
+      if (sweeps >= p->opt.als_sweeps) break;
+    } else if (delta <= p->opt.als_delta || sweeps >= p->opt.als_max_iter) {
+      break;
+    }
+  }
+  // orth: U <- orth([U, u]), V <- orth([V, v])
+  double* uq = p->UU + (size_t)3 * j * ny;
+  double* vq = p->VV + (size_t)3 * j * nx;
+  copy(ny, p->u, uq, st);
+  copy(nx, p->v, vq, st);
+  double ru = 0.0, rv = 0.0;
+  TRY(cgs2(p, ny, p->UU, 3 * (int64_t)ny, j, uq, &ru));
+  TRY(cgs2(p, nx, p->VV, 3 * (int64_t)nx, j, vq, &rv));
+  if (!(ru >= 1e-12) || !(rv >= 1e-12)) return fail(p, CR_ERANK, "new ALS factor lies in the current span");
+  TRY(grow_projections(p, j));
+  zero_border(j, p->Z, p->rcap, st);
+  p->j = j + 1;
+  p->F_valid = false;
+  TRY(sync(p));
+  if (info) {
+    info->rank = p->j;
+    info->sweeps = sweeps;
+    info->delta = delta;
+    info->unorm = un;
+    info->vnorm = vn;
+    info->pcg_iters_u = itu;
+    info->pcg_iters_v = itv;
+    info->pcg_relres_max = worst;
+  }
+  int nc = 0;
+  for (int q = 0; q < 2; ++q) nc += p->hs->stat[q].status == 1;
+  if (nc) return fail(p, CR_ENOTCONV, "PCG reached pcg_maxit (the step was still taken)");
+  return CR_OK;
+}
+
+}  // namespace
+
+// =========================================================================== C ABI
+extern "C" {
+
+cr_status cr_options_default(cr_options* o) {
+  if (!o) return CR_EINVAL;
+  std::memset(o, 0, sizeof(*o));
+  o->struct_size = sizeof(cr_options);
+  o->r_cap = 100;
+  o->precision = CR_FP64;
+  o->precond = CR_PRECOND_JACOBI;
+  o->pcg_tol = 1e-10;
+  o->pcg_maxit = 20000;
+  o->als_delta = 0.1;
+  o->als_max_iter = 10;
+  o->als_sweeps = 0;
+  o->galerkin_maxit = 0;
+  o->residual_every = 1;
+  o->cluster_size = 0;
+  o->seed = 1808;
+  return CR_OK;
+}
+
+double cr_lambda_from_bar(double lambda_bar, int64_t ninj, int64_t nx) {
+  return nx > 0 ? lambda_bar * (double)ninj / (double)nx : NAN;
+}
+
+const char* cr_status_str(cr_status s) {
+  switch (s) {
+    case CR_OK: return "ok";
+    case CR_EINVAL: return "invalid argument";
+    case CR_ENOMEM: return "out of device memory";
+    case CR_ECUDA: return "CUDA error";
+    case CR_ENOTCONV: return "iteration cap reached";
+    case CR_ETIMEOUT: return "time budget exceeded";
+    case CR_ERANK: return "rank deficient update";
+    case CR_ESTATE: return "invalid state";
+  }
+  return "unknown status";
+}
+
+const char* cr_last_error(const cr_problem* p) { return p ? p->err.c_str() : g_create_err.c_str(); }
+
+void cr_destroy(cr_problem* p) {
+  if (!p) return;
+  if (p->st) cudaStreamSynchronize(p->st);
+  for (auto& a : p->allocs) {
+    if (p->opt.alloc)
+      p->opt.free(a.first, a.second, p->opt.alloc_ctx);
+    else
+      cudaFree(a.first);
+  }
+  if (p->hs) cudaFreeHost(p->hs);
+  if (p->own_stream && p->st) cudaStreamDestroy(p->st);
+  delete p;
+}
+
+cr_status cr_create(const cr_problem_desc* d, const cr_options* o, cr_problem** out) {
+  if (out) *out = nullptr;
+  g_create_err.clear();
+  auto bad = [](const std::string& m) {
+    g_create_err = m;
+    return CR_EINVAL;
+  };
+  if (!d || !out) return bad("null argument");
+  cr_options opt;
+  cr_options_default(&opt);
+  if (o) {
+    if (o->struct_size != sizeof(cr_options)) return bad("cr_options.struct_size mismatch");
+    opt = *o;
+  }
+  const int64_t nx = d->nx, ny = d->ny, m = d->ninj;
+  if (nx <= 0 || ny <= 0 || m <= 0 || nx > (1 << 24) || ny > (1 << 24) || m > 4096) return bad("bad sizes");
+  if (!d->X_host || !d->Y_host || !d->Omega_host || d->ldx < nx || d->ldy < ny || d->ldo < ny)
+    return bad("null data pointer or leading dimension too small");
+  if (!(d->lambda > 0.0) || !std::isfinite(d->lambda)) return bad("lambda must be finite and > 0");
+  if (opt.r_cap < 1 || opt.r_cap > std::min(nx, ny)) return bad("r_cap must be in [1, min(nx, ny)]");
+  if (!(opt.pcg_tol > 0.0) || opt.pcg_maxit < 1 || opt.als_max_iter < 1 || !(opt.als_delta >= 0.0))
+    return bad("bad solver options");
+  if (opt.alloc && !opt.free) return bad("alloc given without free");
+  std::string err;
+  if (check_csr(d->Lx, nx, "Lx", err) != CR_OK || check_csr(d->Ly, ny, "Ly", err) != CR_OK) return bad(err);
+  for (int64_t a = 0; a < m; ++a) {
+    for (int64_t i = 0; i < nx; ++i)
+      if (!std::isfinite(d->X_host[i + a * d->ldx])) return bad("X has a non-finite entry");
+    for (int64_t i = 0; i < ny; ++i) {
+      if (!std::isfinite(d->Y_host[i + a * d->ldy])) return bad("Y has a non-finite entry");
+      if (d->Omega_host[i + a * d->ldo] > 1) return bad("Omega entries must be 0 or 1");
+    }
+  }
+
+  cr_problem* p = new cr_problem();
+  p->nx = (int)nx;
+  p->ny = (int)ny;
+  p->m = (int)m;
+  p->rcap = opt.r_cap;
+  p->lam = d->lambda;
+  p->opt = opt;
+  auto abort_create = [&](cr_status s) {
+    g_create_err = p->err;
+    cr_destroy(p);
+    return s;
+  };
+  if (opt.stream) {
+    p->st = (cudaStream_t)opt.stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&p->st, cudaStreamNonBlocking) != cudaSuccess) {
+      p->err = "cudaStreamCreate failed";
+      return abort_create(CR_ECUDA);
+    }
+    p->own_stream = true;
+  }
+  if (cudaMallocHost(&p->hs, sizeof(HostScal)) != cudaSuccess) {
+    p->err = "cudaMallocHost failed";
+    return abort_create(CR_ENOMEM);
+  }
+  cr_status s;
+#define CK(x)                           \
+  do {                                  \
+    if ((s = (x)) != CR_OK) return abort_create(s); \
+  } while (0)
+  CK(build_lap(p, d->Ly, p->Ly));
+  CK(build_lap(p, d->Lx, p->Lx));
+  // X: CSC, CSR by rows, and per-CTA local CSC on the x partition
+  {
+    std::vector<int> cp(m + 1, 0), row;
+    std::vector<double> val;
+    std::vector<std::vector<std::pair<int, double>>> byrow(nx);
+    for (int64_t a = 0; a < m; ++a) {
+      for (int64_t i = 0; i < nx; ++i) {
+        const double x = d->X_host[i + a * d->ldx];
+        if (x != 0.0) {
+          row.push_back((int)i);
+          val.push_back(x);
+          byrow[i].push_back({(int)a, x});
+        }
+      }
+      cp[a + 1] = (int)row.size();
+    }
+    std::vector<int> rp(nx + 1, 0), rc;
+    std::vector<double> rv;
+    for (int64_t i = 0; i < nx; ++i) {
+      for (auto& e : byrow[i]) {
+        rc.push_back(e.first);
+        rv.push_back(e.second);
+      }
+      rp[i + 1] = (int)rc.size();
+    }
+    const int C = p->Lx.csize, chunk = p->Lx.chunk;
+    std::vector<int> lp((size_t)C * m + 1, 0), lr;
+    std::vector<double> lv;
+    for (int r = 0; r < C; ++r)
+      for (int64_t a = 0; a < m; ++a) {
+        for (int q = cp[a]; q < cp[a + 1]; ++q)
+          if (row[q] / chunk == r) {
+            lr.push_back(row[q] - r * chunk);
+            lv.push_back(val[q]);
+          }
+        lp[(size_t)r * m + a + 1] = (int)lr.size();
+      }
+    CK(upload(p, &p->xc_ptr, cp));
+    CK(upload(p, &p->xc_row, row));
+    CK(upload(p, &p->xc_val, val));
+    int *d_rp, *d_rc, *d_lp, *d_lr;
+    double *d_rv, *d_lv;
+    CK(upload(p, &d_rp, rp));
+    CK(upload(p, &d_rc, rc));
+    CK(upload(p, &d_rv, rv));
+    CK(upload(p, &d_lp, lp));
+    CK(upload(p, &d_lr, lr));
+    CK(upload(p, &d_lv, lv));
+    p->xl = DevXLocal{d_lp, d_lr, d_lv, d_rp, d_rc, d_rv};
+  }
+  // Omega o Y, Omega; norms |D|_F (via the m x m Gram products, all terms of
+  // one sign pattern: |D|^2 = tr((OmY^T OmY)(X^T X))) and |Omega o Y|^2
+  std::vector<double> omy((size_t)ny * m);
+  std::vector<uint8_t> om((size_t)ny * m);
+  for (int64_t a = 0; a < m; ++a)
+    for (int64_t i = 0; i < ny; ++i) {
+      om[i + a * ny] = d->Omega_host[i + a * d->ldo];
+      omy[i + a * ny] = om[i + a * ny] ? d->Y_host[i + a * d->ldy] : 0.0;
+    }
+  {
+    std::vector<double> g1((size_t)m * m, 0.0), g2((size_t)m * m, 0.0);
+    for (int64_t a = 0; a < m; ++a)
+      for (int64_t b = 0; b <= a; ++b) {
+        double s1 = 0.0, s2 = 0.0;
+        for (int64_t i = 0; i < ny; ++i) s1 += omy[i + a * ny] * omy[i + b * ny];
+        for (int64_t i = 0; i < nx; ++i) s2 += d->X_host[i + a * d->ldx] * d->X_host[i + b * d->ldx];
+        g1[a + b * m] = g1[b + a * m] = s1;
+        g2[a + b * m] = g2[b + a * m] = s2;
+      }
+    double dn2 = 0.0, on2 = 0.0;
+    for (size_t t = 0; t < g1.size(); ++t) dn2 += g1[t] * g2[t];
+    for (int64_t a = 0; a < m; ++a) on2 += g1[a + a * m];
+    p->Dnorm = std::sqrt(std::max(dn2, 0.0));
+    p->OmYn2 = on2;
+  }
+  CK(upload(p, &p->OmY, omy));
+  CK(upload(p, &p->Om, om));
+  const int rc = p->rcap;
+  const size_t r2 = (size_t)rc * rc;
+  CK(dalloc(p, &p->UU, (size_t)3 * rc * ny));
+  CK(dalloc(p, &p->VV, (size_t)3 * rc * nx));
+  for (double** b : {&p->Z, &p->Zprev, &p->A1, &p->A2, &p->B1, &p->B2, &p->F, &p->gR, &p->gP, &p->gQ, &p->gZB2,
+                     &p->gZB1})
+    CK(dalloc(p, b, r2));
+  for (double** b : {&p->H, &p->P, &p->Mzh, &p->gZH, &p->gGw}) CK(dalloc(p, b, (size_t)rc * m));
+  CK(dalloc(p, &p->G, r2 * m));
+  CK(dalloc(p, &p->E, (size_t)ny * m));
+  CK(dalloc(p, &p->Bnm, (size_t)ny * std::max<int64_t>(m, 1) + (size_t)ny * m));
+  const int nmax = (int)std::max(nx, ny);
+  for (double** b : {&p->u, &p->uhat, &p->rhs_u, &p->tmpy}) CK(dalloc(p, b, ny));
+  for (double** b : {&p->v, &p->vhat, &p->rhs_v, &p->tmpx}) CK(dalloc(p, b, nx));
+  for (double** b : {&p->pr, &p->pp, &p->ps, &p->pw, &p->pdinv, &p->pomt}) CK(dalloc(p, b, nmax));
+  for (double** b : {&p->xi, &p->eta, &p->svec}) CK(dalloc(p, b, m));
+  CK(dalloc(p, &p->hc, (size_t)3 * rc + m));
+  CK(dalloc(p, &p->gc, (size_t)3 * rc + m));
+  CK(dalloc(p, &p->cvec, (size_t)3 * rc + 2 * m));
+  CK(dalloc(p, &p->coef, 8));
+  CK(dalloc(p, &p->stat, 2));
+  CK(dalloc(p, &p->ds, DS_COUNT));
+  // residual-norm bases and core workspaces
+  p->ldcl = 3 * (int64_t)rc;
+  p->ldcr = m + 3 * (int64_t)rc;
+  p->ldcx = 3 * (int64_t)rc;
+  p->ldcp = 3 * (int64_t)rc + m;
+  p->ldm = m + 3 * (int64_t)rc;
+  CK(dalloc(p, &p->QL, (size_t)ny * (3 * rc + m)));
+  CK(dalloc(p, &p->CL, (size_t)p->ldcl * 3 * rc));
+  CK(dalloc(p, &p->QR, (size_t)nx * (3 * rc + m)));
+  CK(dalloc(p, &p->CRm, (size_t)p->ldcr * p->ldcr));
+  CK(dalloc(p, &p->Cx, (size_t)p->ldcx * m));
+  CK(dalloc(p, &p->Cx2, (size_t)p->ldcx * m));
+  CK(dalloc(p, &p->Ep, (size_t)ny * m));
+  CK(dalloc(p, &p->CE, (size_t)m * m));
+  CK(dalloc(p, &p->CP, (size_t)p->ldcp * p->ldm));
+  CK(dalloc(p, &p->Mc, (size_t)p->ldm * p->ldm));
+  CK(dalloc(p, &p->T1, (size_t)p->ldcp * p->ldm));
+  CK(dalloc(p, &p->T2, (size_t)p->ldcp * p->ldm));
+  CK(dalloc(p, &p->gram, (size_t)m * m));
+  CK(dalloc(p, &p->tmat, (size_t)m * m));
+  p->ws_elems = std::max<size_t>((size_t)8 * p->ldcp * p->ldm, (size_t)16 * (3 * rc + m) * m);
+  p->ws_elems = std::max<size_t>(p->ws_elems, (size_t)16 * r2);
+  CK(dalloc(p, &p->ws, p->ws_elems));
+  // right residual basis: X first (host Gram-Schmidt twice, columns in X's span rejected)
+  {
+    std::vector<double> Q((size_t)nx * m, 0.0), Cm((size_t)p->ldcr * m, 0.0);
+    int nq = 0;
+    std::vector<double> w(nx);
+    for (int64_t a = 0; a < m; ++a) {
+      for (int64_t i = 0; i < nx; ++i) w[i] = d->X_host[i + a * d->ldx];
+      double nb = 0.0;
+      for (double x : w) nb += x * x;
+      for (int pass = 0; pass < 2; ++pass)
+        for (int q = 0; q < nq; ++q) {
+          double c = 0.0;
+          for (int64_t i = 0; i < nx; ++i) c += Q[i + (size_t)q * nx] * w[i];
+          for (int64_t i = 0; i < nx; ++i) w[i] -= c * Q[i + (size_t)q * nx];
+        }
+      double na = 0.0;
+      for (double x : w) na += x * x;
+      if (nb > 0.0 && std::sqrt(na / nb) > 1e-12) {
+        const double inv = 1.0 / std::sqrt(na);
+        for (int64_t i = 0; i < nx; ++i) Q[i + (size_t)nq * nx] = w[i] * inv;
+        ++nq;
+      }
+    }
+    for (int64_t a = 0; a < m; ++a)
+      for (int q = 0; q < nq; ++q) {
+        double c = 0.0;
+        for (int64_t i = 0; i < nx; ++i) c += Q[i + (size_t)q * nx] * d->X_host[i + a * d->ldx];
+        Cm[q + (size_t)a * p->ldcr] = c;
+      }
+    CUCHK(p, cudaMemcpyAsync(p->QR, Q.data(), sizeof(double) * nx * nq, cudaMemcpyHostToDevice, p->st));
+    CUCHK(p, cudaMemcpyAsync(p->CRm, Cm.data(), sizeof(double) * Cm.size(), cudaMemcpyHostToDevice, p->st));
+    p->nQR = nq;
+    p->nQX = nq;
+    if (sync(p) != CR_OK) return abort_create(CR_ECUDA);
+  }
+  refresh_E(p);
+  if ((s = sync(p)) != CR_OK) return abort_create(s);
+#undef CK
+  *out = p;
+  return CR_OK;
+}
+
+cr_status cr_add_rank_one(cr_problem* p, cr_rank1_info* info) {
+  if (!p) return CR_EINVAL;
+  return do_rank_one(p, info);
+}
+
+cr_status cr_project(cr_problem* p, double tol, cr_proj_info* info) {
+  if (!p || !(tol >= 0.0)) return CR_EINVAL;
+  return do_project(p, tol, info);
+}
+
+cr_status cr_residual(cr_problem* p, double* relres, double* J, double* dW) {
+  if (!p) return CR_EINVAL;
+  const int j = p->j;
+  const int64_t ld = p->rcap;
+  if (dW) {
+    if (j == 0) {
+      *dW = 0.0;
+    } else {
+      mat_diff_norms(j, p->Z, p->Zprev, ld, p->ds + DS_DW, p->st);
+      TRY(readback(p, DS_DW, 2, false));
+      const double a = p->hs->ds[DS_DW], b = p->hs->ds[DS_DW + 1];
+      *dW = b > 0.0 ? std::sqrt(a / b) : 0.0;
+    }
+  }
+  if (J) {
+    if (j == 0) {
+      *J = 0.5 * p->OmYn2;
+    } else {
+      if (!p->F_valid) build_F(p);
+      galerkin_apply(p, p->Z, p->gQ);
+      mat_dot(j, j, p->Z, ld, p->gQ, ld, p->ds + DS_ZKZ, p->st);
+      mat_dot(j, j, p->Z, ld, p->F, ld, p->ds + DS_ZF, p->st);
+      TRY(readback(p, DS_ZKZ, 2, false));
+      *J = 0.5 * p->hs->ds[DS_ZKZ] - p->hs->ds[DS_ZF] + 0.5 * p->OmYn2;
+    }
+  }
+  if (relres) TRY(do_relres(p, relres));
+  return CR_OK;
+}
+
+cr_status cr_solve(cr_problem* p, int32_t r_max, double tau, double relres_target, cr_solve_info* info) {
+  if (!p || r_max < 0 || !(tau >= 0.0)) return CR_EINVAL;
+  const auto t0 = std::chrono::steady_clock::now();
+  cr_solve_info si{};
+  si.stop = CR_STOP_NONE;
+  si.relres = NAN;
+  si.dW = NAN;
+  cr_status rc = CR_OK;
+  int step = 0;
+  while (p->j < std::min(r_max, p->rcap)) {
+    cr_rank1_info ri{};
+    cr_status s = do_rank_one(p, &ri);
+    si.pcg_iters += ri.pcg_iters_u + ri.pcg_iters_v;
+    if (s == CR_ERANK) {
+      si.stop = CR_STOP_RANK;
+      break;
+    }
+    if (s != CR_OK && s != CR_ENOTCONV) return s;
+    if (s == CR_ENOTCONV) rc = s;
+    cr_proj_info pi{};
+    s = do_project(p, tau / 2.0, &pi);
+    si.cg_iters += pi.iters;
+    if (s != CR_OK && s != CR_ENOTCONV) return s;
+    if (s == CR_ENOTCONV) rc = s;
+    ++step;
+    double dW = 0.0;
+    double* rr = nullptr;
+    double relres = NAN;
+    if (relres_target > 0.0 && (step % std::max(1, p->opt.residual_every) == 0 || p->j >= r_max)) rr = &relres;
+    TRY(cr_residual(p, rr, nullptr, &dW));
+    si.dW = dW;
+    if (rr) si.relres = relres;
+    if (dW <= tau) {
+      si.stop = CR_STOP_DW;
+      break;
+    }
+    if (rr && relres <= relres_target) {
+      si.stop = CR_STOP_RELRES;
+      break;
+    }
+  }
+  if (si.stop == CR_STOP_NONE) si.stop = CR_STOP_RMAX;
+  si.rank = p->j;
+  double J = NAN;
+  TRY(cr_residual(p, std::isnan(si.relres) ? &si.relres : nullptr, &J, nullptr));
+  si.J = J;
+  si.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = si;
+  return rc;
+}
+
+cr_status cr_get_rank(const cr_problem* p, int32_t* j) {
+  if (!p || !j) return CR_EINVAL;
+  *j = p->j;
+  return CR_OK;
+}
+
+cr_status cr_get_factors(cr_problem* p, double* U, int64_t ldu, double* Zh, int64_t ldz, double* V, int64_t ldv) {
+  if (!p) return CR_EINVAL;
+  const int j = p->j;
+  if (j == 0) return CR_OK;
+  if ((U && ldu < p->ny) || (Zh && ldz < j) || (V && ldv < p->nx)) return fail(p, CR_EINVAL, "leading dimension");
+  if (U)
+    CUCHK(p, cudaMemcpy2DAsync(U, ldu * sizeof(double), p->UU, 3 * (size_t)p->ny * sizeof(double),
+                               p->ny * sizeof(double), j, cudaMemcpyDeviceToHost, p->st));
+  if (V)
+    CUCHK(p, cudaMemcpy2DAsync(V, ldv * sizeof(double), p->VV, 3 * (size_t)p->nx * sizeof(double),
+                               p->nx * sizeof(double), j, cudaMemcpyDeviceToHost, p->st));
+  if (Zh)
+    CUCHK(p, cudaMemcpy2DAsync(Zh, ldz * sizeof(double), p->Z, (size_t)p->rcap * sizeof(double), j * sizeof(double),
+                               j, cudaMemcpyDeviceToHost, p->st));
+  return sync(p);
+}
+
+cr_status cr_set_factors(cr_problem* p, int32_t j, const double* U, int64_t ldu, const double* Zh, int64_t ldz,
+                         const double* V, int64_t ldv) {
+  if (!p) return CR_EINVAL;
+  if (j < 0 || j > p->rcap) return fail(p, CR_EINVAL, "rank outside [0, r_cap]");
+  if (j > 0 && (!U || !Zh || !V || ldu < p->ny || ldz < j || ldv < p->nx))
+    return fail(p, CR_EINVAL, "null factor or leading dimension too small");
+  cudaStream_t st = p->st;
+  const int64_t ld = p->rcap;
+  fill((int64_t)ld * ld, 0.0, p->Z, st);
+  fill((int64_t)p->ldcl * 3 * ld, 0.0, p->CL, st);
+  fill((int64_t)p->ldcr * p->ldcr - (int64_t)p->ldcr * p->m, 0.0, p->CRm + (size_t)p->ldcr * p->m, st);
+  p->nQL = 0;
+  p->nQR = p->nQX;  // the X part of the right basis does not depend on the factors
+  p->j = 0;
+  if (j > 0) {
+    CUCHK(p, cudaMemcpy2DAsync(p->UU, 3 * (size_t)p->ny * sizeof(double), U, ldu * sizeof(double),
+                               p->ny * sizeof(double), j, cudaMemcpyHostToDevice, st));
+    CUCHK(p, cudaMemcpy2DAsync(p->VV, 3 * (size_t)p->nx * sizeof(double), V, ldv * sizeof(double),
+                               p->nx * sizeof(double), j, cudaMemcpyHostToDevice, st));
+    CUCHK(p, cudaMemcpy2DAsync(p->Z, ld * sizeof(double), Zh, ldz * sizeof(double), j * sizeof(double), j,
+                               cudaMemcpyHostToDevice, st));
+    for (int q = 0; q < j; ++q) TRY(grow_projections(p, q));
+  }
+  p->j = j;
+  CUCHK(p, cudaMemcpyAsync(p->Zprev, p->Z, sizeof(double) * ld * ld, cudaMemcpyDeviceToDevice, st));
+  build_F(p);
+  refresh_E(p);
+  return sync(p);
+}
+
+cr_status cr_apply_residual(cr_problem* p, int32_t trans, const double* in, double* out) {
+  if (!p || !in || !out) return CR_EINVAL;
+  cudaStream_t st = p->st;
+  if (!trans) {
+    CUCHK(p, cudaMemcpyAsync(p->tmpx, in, sizeof(double) * p->nx, cudaMemcpyHostToDevice, st));
+    residual_times(p, p->tmpx, p->rhs_u);
+    CUCHK(p, cudaMemcpyAsync(out, p->rhs_u, sizeof(double) * p->ny, cudaMemcpyDeviceToHost, st));
+  } else {
+    CUCHK(p, cudaMemcpyAsync(p->tmpy, in, sizeof(double) * p->ny, cudaMemcpyHostToDevice, st));
+    residual_t_times(p, p->tmpy, p->rhs_v);
+    CUCHK(p, cudaMemcpyAsync(out, p->rhs_v, sizeof(double) * p->nx, cudaMemcpyDeviceToHost, st));
+  }
+  return sync(p);
+}
+
+cr_status cr_solve_u(cr_problem* p, const double* v, const double* rhs, double* uh, int32_t* iters) {
+  if (!p || !v || !rhs || !uh) return CR_EINVAL;
+  cudaStream_t st = p->st;
+  CUCHK(p, cudaMemcpyAsync(p->v, v, sizeof(double) * p->nx, cudaMemcpyHostToDevice, st));
+  CUCHK(p, cudaMemcpyAsync(p->rhs_u, rhs, sizeof(double) * p->ny, cudaMemcpyHostToDevice, st));
+  prep_u(p, p->v);
+  fill(p->ny, 0.0, p->uhat, st);
+  TRY(launch_pcg(p, 0, p->rhs_u, p->uhat));
+  CUCHK(p, cudaMemcpyAsync(uh, p->uhat, sizeof(double) * p->ny, cudaMemcpyDeviceToHost, st));
+  TRY(readback(p, 0, 1, true));
+  if (iters) *iters = p->hs->stat[0].iters;
+  if (p->hs->stat[0].status == 2) return fail(p, CR_ENOTCONV, "PCG breakdown");
+  if (p->hs->stat[0].status == 1) return fail(p, CR_ENOTCONV, "PCG reached pcg_maxit");
+  return CR_OK;
+}
+
+cr_status cr_solve_v(cr_problem* p, const double* u, const double* rhs, double* vh, int32_t* iters) {
+  if (!p || !u || !rhs || !vh) return CR_EINVAL;
+  cudaStream_t st = p->st;
+  CUCHK(p, cudaMemcpyAsync(p->u, u, sizeof(double) * p->ny, cudaMemcpyHostToDevice, st));
+  CUCHK(p, cudaMemcpyAsync(p->rhs_v, rhs, sizeof(double) * p->nx, cudaMemcpyHostToDevice, st));
+  prep_v(p, p->u);
+  fill(p->nx, 0.0, p->vhat, st);
+  TRY(launch_pcg(p, 1, p->rhs_v, p->vhat));
+  CUCHK(p, cudaMemcpyAsync(vh, p->vhat, sizeof(double) * p->nx, cudaMemcpyDeviceToHost, st));
+  TRY(readback(p, 0, 1, true));
+  if (iters) *iters = p->hs->stat[1].iters;
+  if (p->hs->stat[1].status == 2) return fail(p, CR_ENOTCONV, "PCG breakdown");
+  if (p->hs->stat[1].status == 1) return fail(p, CR_ENOTCONV, "PCG reached pcg_maxit");
+  return CR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,167 @@
+// Internal declarations shared by the CUDA translation units of libconreg.
+//
+// Device data layout (all float64 unless noted, column-major):
+//   UU (ny x 3 r_cap): column 3p+s holds L_y^s u_p (s = 0, 1, 2); VV likewise
+//   for v_p and L_x.  Interleaving puts every factor block that the residual
+//   products and the residual norm need (Sec. 2.3: R_j v, R_j^T u) into one
+//   contiguous panel, so each of them is a single panel-times-vector pass.
+//   E (ny x m) = Omega o (Y - U Z V^T X): the masked data residual, refreshed
+//   once per projection; R_j v = E (X^T v) - UU g(v) with a 3j coefficient
+//   vector g (see cr_api.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+namespace cr {
+
+constexpr int kMaxSlots = 16;     // off-diagonal entries per Laplacian row
+constexpr int kPcgThreads = 512;  // threads per CTA of the cluster PCG
+constexpr int kMaxCluster = 16;
+
+// Sparse symmetric matrix in padded ELL form ("slot-major": slot k of row i at
+// [k * n + i]); the diagonal is kept apart.  Graph Laplacians with unit weights
+// store no off-diagonal values (offw == nullptr; every stored neighbour has
+// weight -1).  For the cluster PCG the neighbour of slot k is also stored
+// packed as (cta_rank << 24) | local_index for the partition of the rows into
+// contiguous chunks of `chunk` rows, one chunk per CTA of a cluster of `csize`.
+struct DevLap {
+  int n = 0;
+  int K = 0;                     // slots per row (padded entries are -1)
+  const int* nbr = nullptr;      // [K * n] global column, -1 = none
+  const int* nbrp = nullptr;     // [K * n] packed (rank, local), -1 = none
+  const double* offw = nullptr;  // [K * n] or nullptr (unit Laplacian)
+  const double* diag = nullptr;  // [n]  L_ii
+  const double* l2diag = nullptr;// [n]  (L^2)_ii = L_ii^2 + sum_k L_ik^2
+  int chunk = 0;                 // rows per CTA
+  int csize = 1;                 // CTAs per cluster
+};
+
+// X restricted to the rows owned by each CTA of the PCG partition (v side):
+// for CTA r and injection a, entries lx_ptr[r*m + a] .. lx_ptr[r*m + a + 1] - 1
+// hold (local row, value).  Plus the CSR of X by row (global rows).
+struct DevXLocal {
+  const int* lx_ptr = nullptr;
+  const int* lx_row = nullptr;
+  const double* lx_val = nullptr;
+  const int* xr_ptr = nullptr;   // [nx + 1]
+  const int* xr_col = nullptr;
+  const double* xr_val = nullptr;
+};
+
+// Scalars the host reads back after a PCG solve.
+struct PcgStat {
+  int iters;
+  int status;      // 0 ok, 1 hit maxit, 2 breakdown
+  double relres;   // recursive residual estimate at exit
+  double bnorm;
+};
+
+// One PCG solve with the operator  lam * [(L + c I)^2 + e I] + data,  where
+// c = coef[0], e = coef[1] - coef[0]^2 (both read on the device), and
+//   data = diag(omega_tilde),  omega_tilde_i = sum_a Om[i + a ldo] * xi[a]^2   (u side, Eq. ALS_linsys)
+//   data = X diag(s) X^T                                                        (v side, Eq. ALS_linsys_v)
+struct PcgArgs {
+  DevLap L;
+  double lam;
+  const double* coef;      // device [2]: (c, d)
+  int m;
+  const uint8_t* Om;       // u side
+  int64_t ldo;
+  const double* xi;        // u side: device [m]
+  DevXLocal X;             // v side
+  const double* s;         // v side: device [m]
+  const double* b;         // rhs [n]
+  double* x;               // in: x0, out: solution [n]
+  double* r;               // work [n]
+  double* p;               // work [n]
+  double* sv;              // work [n]
+  double* w;               // work [n]
+  double* dinv;            // work [n]
+  double* omt;             // work [n] (u side)
+  double tol;
+  int maxit;
+  PcgStat* stat;           // device
+};
+
+// ---------------------------------------------------------------- cr_pcg.cu
+cudaError_t pcg_launch(const PcgArgs& a, int data_kind, cudaStream_t st);
+cudaError_t pcg_prepare(int data_kind, int csize, size_t smem_bytes);
+size_t pcg_smem_bytes(int chunk, int m);
+bool pcg_cluster_ok(int csize, size_t smem_bytes);
+// y = (L + shift I) x
+void lap_apply(const DevLap& L, const double* x, double* y, double shift, cudaStream_t st);
+
+// ---------------------------------------------------------------- cr_blas.cu
+// Strided matrix view: element (i, k) at ptr[i * si + k * sk].
+struct MatView {
+  const double* ptr;
+  int64_t si, sk;
+};
+
+// C(i, l) = alpha * sum_k A(i, k) B(k, l) + beta * C(i, l), for i < M, l < N,
+// k < K.  Deterministic: K is split in a fixed number of ranges whose partial
+// sums are added in order.  ws must hold splits * M * N doubles (see gemm_ws).
+void gemm(int M, int N, int K, double alpha, MatView A, MatView B, double beta, double* C, int64_t sci,
+          int64_t scl, double* ws, size_t ws_elems, cudaStream_t st);
+
+// out[p * ostride] = alpha * sum_i A[i + p*lda] * w[i] (+ beta * out), p < k; one warp per column.
+void gemv_t(int n, int k, const double* A, int64_t lda, const double* w, double* out, int64_t ostride,
+            double alpha, double beta, cudaStream_t st);
+// y[i] = beta * y[i] + alpha * sum_p A[i + p*lda] * c[p*cstride]
+void gemv_n(int n, int k, const double* A, int64_t lda, const double* c, int64_t cstride, double* y,
+            double alpha, double beta, cudaStream_t st);
+// out = alpha * sum_i x[i] * y[i] into *out (single deterministic reduction)
+void dot(int n, const double* x, const double* y, double* out, cudaStream_t st);
+// out[a * ostride] = sum over the nonzeros of column a of X (CSC) of X_ka * v[k]
+void spmv_xt(int m, const int* colptr, const int* row, const double* val, const double* v, double* out,
+             int64_t ostride, cudaStream_t st);
+// y[k] = beta*y[k] + alpha * sum_a X_ka * c[a], X by rows (CSR)
+void spmv_x(int n, const int* rowptr, const int* col, const double* val, const double* c, double* y,
+            double alpha, double beta, cudaStream_t st);
+// out[a] = sum_i Om[i + a*ldo] * u[i]^2
+void omega_sq_dots(int n, int m, const uint8_t* Om, int64_t ldo, const double* u, double* out,
+                   cudaStream_t st);
+// y = x * (1 / *nrm) ; *nrm computed on the device (sqrt of a dot)
+void scale_by_inv_norm(int n, const double* x, const double* nrm2, double* y, cudaStream_t st);
+void copy(int n, const double* x, double* y, cudaStream_t st);
+void fill(int64_t n, double v, double* y, cudaStream_t st);
+
+// Galerkin-specific kernels
+// g_a = G_a w_a for a < m: G (m blocks of ld_g x ld_g, block a at G + a*gstride), w (j x m, ld ldw)
+void batched_gemv(int j, int m, const double* G, int64_t ldg, int64_t gstride, const double* w, int64_t ldw,
+                  double* out, int64_t ldo, cudaStream_t st);
+
+}  // namespace cr
+
+namespace cr {
+// ---------------------------------------------------------------- cr_small.cu
+// g[3p+s] = coef_s * sum_q Zop(p, q) h[3q + 2 - s], coef = (lam, 2 lam, lam), Zop = Z or Z^T
+void zcoef(int j, const double* Z, int64_t ldz, int trans, const double* h, double lam, double* g, cudaStream_t st);
+// A(col, p) = A(p, col) for p < col, in `batch` matrices spaced `stride` apart
+void mirror_col(int col, double* A, int64_t ld, int batch, int64_t stride, cudaStream_t st);
+// Z(j, q) = Z(q, j) = 0 for q <= j
+void zero_border(int j, double* Z, int64_t ld, cudaStream_t st);
+// E = OmY - Om o E  (ny x m, ld ny)
+void mask_residual(int n, int m, const double* OmY, const uint8_t* Om, int64_t ldo, double* E, cudaStream_t st);
+// B(i, a) = Om(i, a) * u(i)
+void omega_times(int n, int m, const uint8_t* Om, int64_t ldo, const double* u, double* B, cudaStream_t st);
+// out[0] = sum_{i<r, l<c} A(i,l) B(i,l) (single deterministic reduction)
+void mat_dot(int r, int c, const double* A, int64_t lda, const double* B, int64_t ldb, double* out, cudaStream_t st);
+// out[0] = |Z - Zp|_F^2, out[1] = |Z|_F^2 over j x j
+void mat_diff_norms(int j, const double* Z, const double* Zp, int64_t ld, double* out, cudaStream_t st);
+// C = alpha A + beta B (r x c); B may alias C
+void mat_axpby(int r, int c, double alpha, const double* A, int64_t lda, double beta, const double* B, int64_t ldb,
+               double* C, int64_t ldc, cudaStream_t st);
+// dst(i, l) = src(i, l)
+void copy2d(int r, int c, const double* src, int64_t lds, double* dst, int64_t ldd, cudaStream_t st);
+// Galerkin CG updates with device scalars gs: rho_k = gs[k & 1], pq = gs[2]
+void cg_update_zr(int j, double* Z, double* R, const double* P, const double* Q, int64_t ld, const double* gs, int k,
+                  cudaStream_t st);
+void cg_update_p(int j, double* P, const double* R, int64_t ld, const double* gs, int k, cudaStream_t st);
+// Core of the residual norm: M (n x n, n = m + 3j): identity on the first m
+// columns, and for the factor block (3p+s, 3q+t): -lam Z(p,q) for (s,t)=(0,2),
+// -2 lam Z(p,q) for (1,1), -lam Z(p,q) for (2,0).
+void build_core(int m, int j, const double* Z, int64_t ldz, double lam, double* Mc, int64_t ldm, cudaStream_t st);
+}  // namespace cr

@@ -1,0 +1,353 @@
+// Cluster-resident preconditioned CG for the ALS sub-problems (Sec. 2.3,
+// Eqs. ALS_linsys and ALS_linsys_v).
+//
+// Both operators have the form  lam * [(L + c I)^2 + e I] + data:
+//   A_hat = lam((v'L_x^2 v) I + 2 (v'L_x v) L_y + L_y^2) + sum_a diag(Omega_a)(v'X_a)^2
+//         = lam[(L_y + cI)^2 + (d - c^2) I] + diag(omega_tilde),  c = v'L_x v, d = |L_x v|^2
+//   B_hat = lam(L_x^2 + 2 (u'L_y u) L_x + (u'L_y^2 u) I) + sum_a (u'diag(Omega_a)u) X_a X_a'
+//         = lam[(L_x + c'I)^2 + (d' - c'^2) I] + X diag(s) X',  c' = u'L_y u, d' = |L_y u|^2
+// so one apply is two sparse stencil passes through an intermediate t = (L + cI) p.
+//
+// Design: one thread-block cluster owns the whole solve.  The rows are split
+// into contiguous chunks, one per CTA; the vector being multiplied and the
+// intermediate t live in shared memory and neighbours owned by other CTAs are
+// read through distributed shared memory.  The iteration is the
+// Chronopoulos-Gear form of PCG, whose three inner products (r,u), (u,w),
+// (r,r) share one reduction, so an iteration costs three cluster barriers and
+// no kernel launch.  Reductions have a fixed order (warp shuffle tree, then
+// warps, then CTAs in rank order), so every CTA computes bit-identical scalars
+// and takes the same branch; results are reproducible run to run.  The loop
+// is bounded by maxit.
+#include <cooperative_groups.h>
+
+#include "cr_common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace cr {
+
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum NV per-thread values over the CTA; thread 0 stores the sums in out[].
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* scr, double* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) scr[wid * NV + q] = v[q];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double t = lane < nw ? scr[lane * NV + q] : 0.0;
+      t = warp_sum(t);
+      if (lane == 0) out[q] = t;
+    }
+  }
+}
+
+// After a cluster barrier: add the NV partials of all CTAs in rank order and
+// broadcast them to the CTA through scal[].
+template <int NV>
+__device__ __forceinline__ void cluster_sum(cg::cluster_group& cl, double* red, double* scal, int csize) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (wid == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double t = 0.0;
+      if (lane < csize) t = cl.map_shared_rank(red, lane)[q];
+      t = warp_sum(t);
+      if (lane == 0) scal[q] = t;
+    }
+  }
+  __syncthreads();
+}
+
+// (L + shift I) applied to row i of a vector held in distributed shared memory.
+__device__ __forceinline__ double lap_row_dsm(const DevLap& L, int i, double vi, double shift, double* buf,
+                                              cg::cluster_group& cl) {
+  double acc = (L.diag[i] + shift) * vi;
+  for (int k = 0; k < L.K; ++k) {
+    const int q = __ldg(L.nbrp + (size_t)k * L.n + i);
+    if (q < 0) continue;
+    const double nv = cl.map_shared_rank(buf, (unsigned)(q >> 24))[q & 0xFFFFFF];
+    acc += (L.offw ? __ldg(L.offw + (size_t)k * L.n + i) : -1.0) * nv;
+  }
+  return acc;
+}
+
+template <int KIND>
+struct Pcg {
+  // t = (L + cI) ub on the owned rows; v side: partial X^T ub of the owned rows.
+  static __device__ __forceinline__ void phase_t(const PcgArgs& A, cg::cluster_group& cl, int beg, int nloc,
+                                                 double c, double* ub, double* tb, double* ypart) {
+    for (int li = threadIdx.x; li < nloc; li += blockDim.x) tb[li] = lap_row_dsm(A.L, beg + li, ub[li], c, ub, cl);
+    if (KIND == 1) {
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+      const int rank = (int)cl.block_rank();
+      for (int a = wid; a < A.m; a += nw) {
+        const int p0 = A.X.lx_ptr[rank * A.m + a], p1 = A.X.lx_ptr[rank * A.m + a + 1];
+        double acc = 0.0;
+        for (int p = p0 + lane; p < p1; p += 32) acc += A.X.lx_val[p] * ub[A.X.lx_row[p]];
+        acc = warp_sum(acc);
+        if (lane == 0) ypart[a] = acc;
+      }
+    }
+  }
+  // v side: y = X^T ub summed over the cluster; sy[a] = s[a] * y[a].
+  static __device__ __forceinline__ void gather_y(const PcgArgs& A, cg::cluster_group& cl, double* ypart,
+                                                  const double* sS, double* sY) {
+    if (KIND == 1) {
+      const int C = (int)cl.num_blocks();
+      for (int a = threadIdx.x; a < A.m; a += blockDim.x) {
+        double t = 0.0;
+        for (int r = 0; r < C; ++r) t += cl.map_shared_rank(ypart, (unsigned)r)[a];
+        sY[a] = sS[a] * t;
+      }
+      __syncthreads();
+    }
+  }
+  // w_i = lam[(L + cI) t + e u]_i + data_i
+  static __device__ __forceinline__ double row_w(const PcgArgs& A, cg::cluster_group& cl, int i, int li, double c,
+                                                 double e, double ui, double* tb, const double* sY) {
+    double w = A.lam * (lap_row_dsm(A.L, i, tb[li], c, tb, cl) + e * ui);
+    if (KIND == 0) {
+      w += A.omt[i] * ui;
+    } else {
+      for (int p = A.X.xr_ptr[i]; p < A.X.xr_ptr[i + 1]; ++p) w += A.X.xr_val[p] * sY[A.X.xr_col[p]];
+    }
+    return w;
+  }
+};
+
+template <int KIND>
+__global__ void __launch_bounds__(kPcgThreads, 1) pcg_cluster_kernel(const PcgArgs A) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const DevLap& L = A.L;
+  const int chunk = L.chunk;
+  const int beg = rank * chunk;
+  const int nloc = max(0, min(L.n - beg, chunk));
+  const int m = A.m;
+  extern __shared__ __align__(16) double sm[];
+  double* ub0 = sm;
+  double* ub1 = sm + chunk;
+  double* tb = sm + 2 * chunk;
+  double* red = tb + chunk;   // [8]
+  double* ypart = red + 8;    // [m]
+  double* sS = ypart + m;     // [m]  xi^2 (u side) or s (v side)
+  double* sY = sS + m;        // [m]  s * (X^T p) (v side)
+  double* scr = sY + m;       // [32 * 4]
+  double* scal = scr + 128;   // [8]
+  const double lam = A.lam;
+  const double c = A.coef[0];
+  const double d = A.coef[1];
+  const double e = d - c * c;
+  using K = Pcg<KIND>;
+
+  for (int a = threadIdx.x; a < m; a += blockDim.x) sS[a] = KIND == 0 ? A.xi[a] * A.xi[a] : A.s[a];
+  __syncthreads();
+  // data term diagonal, Jacobi preconditioner, initial guess into shared memory
+  for (int li = threadIdx.x; li < nloc; li += blockDim.x) {
+    const int i = beg + li;
+    double dd = lam * (L.l2diag[i] + 2.0 * c * L.diag[i] + d);
+    if (KIND == 0) {
+      double o = 0.0;
+      for (int a = 0; a < m; ++a) o += (double)A.Om[i + (int64_t)a * A.ldo] * sS[a];
+      A.omt[i] = o;
+      dd += o;
+    } else {
+      for (int p = A.X.xr_ptr[i]; p < A.X.xr_ptr[i + 1]; ++p) dd += A.X.xr_val[p] * A.X.xr_val[p] * sS[A.X.xr_col[p]];
+    }
+    A.dinv[i] = dd > 0.0 ? 1.0 / dd : 1.0;
+    ub0[li] = A.x[i];
+  }
+  cl.sync();
+  K::phase_t(A, cl, beg, nloc, c, ub0, tb, ypart);
+  cl.sync();
+  K::gather_y(A, cl, ypart, sS, sY);
+  {
+    double v[1] = {0.0};
+    for (int li = threadIdx.x; li < nloc; li += blockDim.x) {
+      const int i = beg + li;
+      const double bi = A.b[i];
+      A.r[i] = bi - K::row_w(A, cl, i, li, c, e, ub0[li], tb, sY);
+      v[0] += bi * bi;
+    }
+    block_sum<1>(v, scr, red);
+  }
+  cl.sync();
+  cluster_sum<1>(cl, red, scal, C);
+  const double bb = scal[0];
+  int it = 0, status = 0;
+  double rho = 0.0;
+  if (bb == 0.0) {
+    for (int li = threadIdx.x; li < nloc; li += blockDim.x) A.x[beg + li] = 0.0;
+  } else {
+    const double tol2 = A.tol * A.tol * bb;
+    double gam_prev = 1.0, alpha_prev = 1.0;
+    int cur = 1;
+    for (;;) {
+      double* ub = cur ? ub1 : ub0;
+      for (int li = threadIdx.x; li < nloc; li += blockDim.x) {
+        const int i = beg + li;
+        ub[li] = A.r[i] * A.dinv[i];
+      }
+      cl.sync();
+      K::phase_t(A, cl, beg, nloc, c, ub, tb, ypart);
+      cl.sync();
+      K::gather_y(A, cl, ypart, sS, sY);
+      double v[3] = {0.0, 0.0, 0.0};
+      for (int li = threadIdx.x; li < nloc; li += blockDim.x) {
+        const int i = beg + li;
+        const double ui = ub[li];
+        const double wi = K::row_w(A, cl, i, li, c, e, ui, tb, sY);
+        const double ri = A.r[i];
+        A.w[i] = wi;
+        v[0] += ri * ui;
+        v[1] += ui * wi;
+        v[2] += ri * ri;
+      }
+      block_sum<3>(v, scr, red);
+      cl.sync();
+      cluster_sum<3>(cl, red, scal, C);
+      const double gam = scal[0], del = scal[1];
+      rho = scal[2];
+      if (rho <= tol2) break;
+      if (it >= A.maxit) { status = 1; break; }
+      double alpha;
+      if (it == 0) {
+        if (!(del > 0.0)) { status = 2; break; }
+        alpha = gam / del;
+        for (int li = threadIdx.x; li < nloc; li += blockDim.x) {
+          const int i = beg + li;
+          const double pi = ub[li], si = A.w[i];
+          A.p[i] = pi;
+          A.sv[i] = si;
+          A.x[i] += alpha * pi;
+          A.r[i] -= alpha * si;
+        }
+      } else {
+        const double beta = gam / gam_prev;
+        const double den = del - beta * gam / alpha_prev;
+        if (!(den > 0.0) || !isfinite(den)) { status = 2; break; }
+        alpha = gam / den;
+        for (int li = threadIdx.x; li < nloc; li += blockDim.x) {
+          const int i = beg + li;
+          const double pi = ub[li] + beta * A.p[i];
+          const double si = A.w[i] + beta * A.sv[i];
+          A.p[i] = pi;
+          A.sv[i] = si;
+          A.x[i] += alpha * pi;
+          A.r[i] -= alpha * si;
+        }
+      }
+      gam_prev = gam;
+      alpha_prev = alpha;
+      cur ^= 1;
+      ++it;
+    }
+  }
+  // No CTA may leave while another can still read its shared memory.
+  cl.sync();
+  if (rank == 0 && threadIdx.x == 0) {
+    A.stat->iters = it;
+    A.stat->status = status;
+    A.stat->relres = bb > 0.0 ? sqrt(rho / bb) : 0.0;
+    A.stat->bnorm = sqrt(bb);
+  }
+}
+
+__global__ void lap_apply_kernel(const DevLap L, const double* __restrict__ x, double* __restrict__ y,
+                                 double shift) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L.n) return;
+  double acc = (L.diag[i] + shift) * x[i];
+  for (int k = 0; k < L.K; ++k) {
+    const int q = L.nbr[(size_t)k * L.n + i];
+    if (q < 0) continue;
+    acc += (L.offw ? L.offw[(size_t)k * L.n + i] : -1.0) * x[q];
+  }
+  y[i] = acc;
+}
+
+}  // namespace
+
+size_t pcg_smem_bytes(int chunk, int m) { return sizeof(double) * (3 * (size_t)chunk + 8 + 3 * (size_t)m + 128 + 8); }
+
+cudaError_t pcg_prepare(int /*data_kind*/, int csize, size_t /*smem_bytes*/) {
+  // the attribute is per kernel, shared by the x and y grids: allow the maximum
+  const size_t smem_bytes = 227 * 1024;
+  cudaError_t e;
+  for (int kind = 0; kind < 2; ++kind) {
+    const void* fn = kind == 0 ? (const void*)pcg_cluster_kernel<0> : (const void*)pcg_cluster_kernel<1>;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    if (e != cudaSuccess) return e;
+    if (csize > 8) {
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+bool pcg_cluster_ok(int cs, size_t smem_bytes) {
+  if (pcg_prepare(0, cs, smem_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cs);
+  cfg.blockDim = dim3(kPcgThreads);
+  cfg.dynamicSmemBytes = smem_bytes;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cs;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  for (int kind = 0; kind < 2; ++kind) {
+    const void* fn = kind == 0 ? (const void*)pcg_cluster_kernel<0> : (const void*)pcg_cluster_kernel<1>;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess || nclusters < 1) {
+      cudaGetLastError();
+      return false;
+    }
+  }
+  return true;
+}
+
+cudaError_t pcg_launch(const PcgArgs& a, int data_kind, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(a.L.csize);
+  cfg.blockDim = dim3(kPcgThreads);
+  cfg.dynamicSmemBytes = pcg_smem_bytes(a.L.chunk, a.m);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = a.L.csize;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (data_kind == 0) return cudaLaunchKernelEx(&cfg, pcg_cluster_kernel<0>, a);
+  return cudaLaunchKernelEx(&cfg, pcg_cluster_kernel<1>, a);
+}
+
+void lap_apply(const DevLap& L, const double* x, double* y, double shift, cudaStream_t st) {
+  if (L.n == 0) return;
+  lap_apply_kernel<<<(L.n + 255) / 256, 256, 0, st>>>(L, x, y, shift);
+}
+
+}  // namespace cr
