@@ -1,0 +1,330 @@
+#!/usr/bin/env python
+"""Benchmark of the greedy low-rank connectome-regression solver on GB300.
+
+One step = one complete run of Algorithm 1 (ALS rank-one updates with PCG
+sub-solves, orthogonalisation, Galerkin projection, residual and stopping test)
+from W = 0 up to relres <= target, dW <= tau or r_max, on the visual-cortex-
+shaped synthetic workload (~7,500 voxels in a smooth random blob mask of a 40^3
+box, 7-point Laplacians, 28 Gaussian injections, lambda = 100, rank <= 100).
+
+Reported: rank-1 updates per second (whole job, all GPUs), the time to the
+relative residual target when reached, an end-to-end number through the public
+API with host buffers, the roofline of the dominant kernel (the cluster PCG),
+the CPU float64 oracle as a baseline, SM clocks during the timed region, and
+the number of library kernel launches.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 (torchrun, one process per GPU) every rank solves its own replica
+of the workload (a single greedy solve does not shard) and rank 0
+reports the aggregate over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-rel-residual 1e-6 and rank-1 updates/s, mixed/learned vs plain FP64 GPU"
+UNIT = "rank-1 updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--lam", type=float, default=1e2)
+    ap.add_argument("--r-max", type=int, default=100)
+    ap.add_argument("--tau", type=float, default=1e-9)
+    ap.add_argument("--relres", type=float, default=1e-6)
+    ap.add_argument("--precision", default="fp64", choices=["fp64"])
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args, rank=0):
+    from paper_1808_05510_gb300 import synth
+
+    p = synth.visual_cortex(seed=1810 + rank, lam=args.lam, r_max=args.r_max)
+    cfg = {
+        "workload": "visual-cortex-shaped synthetic: smooth random blob mask in a 40^3 box, 7-point Laplacians",
+        "ny": p.ny, "nx": p.nx, "ninj": p.m, "lambda": p.lam, "r_max": args.r_max, "tau": args.tau,
+        "relres_target": args.relres, "precision": args.precision,
+        "l2": "flushed between steps (256 MiB write)", "parallelism": "replicas",
+    }
+    return p, cfg
+
+
+# ----------------------------------------------------------------------------- helpers
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = threading.Thread(target=self._run, daemon=True)
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if len(s) > 5 + k and "Active" in s[5 + k]
+                          and "Not" not in s[5 + k]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def flush_l2(buf):
+    buf.add_(1.0)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "of measured"
+    except Exception:
+        return 6800.0, "of fallback"
+
+
+def pcg_bytes_per_iter(n: int, slots: int = 6) -> float:
+    """Algorithmic bytes of one float64 Chronopoulos-Gear PCG iteration: read and
+    write r, x, p, s (64 B), read the Jacobi diagonal and the data diagonal
+    (16 B), read the neighbour table once (4 B per slot)."""
+    return n * (64.0 + 16.0 + 4.0 * slots)
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_sample(p, args, seconds: float):
+    """The CPU float64 oracle (Algorithm 1, its own CG sub-solves) on a bounded
+    sample: greedy steps from W = 0 until `seconds` of work; rank-1 updates/s."""
+    from oracle import Oracle
+
+    class Stop(Exception):
+        pass
+
+    o = Oracle.from_problem(p, cg_tol=1e-10)
+    t0 = time.perf_counter()
+    done = [0]
+
+    def cb(st, U, Z, V):
+        done[0] = st.j
+        if time.perf_counter() - t0 > seconds:
+            raise Stop()
+
+    try:
+        o.greedy(r_max=args.r_max, tau=args.tau, relres_target=args.relres, callback=cb)
+    except Stop:
+        pass
+    el = time.perf_counter() - t0
+    cores = os.cpu_count()
+    return {"value": done[0] / el if el > 0 else None, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {done[0]} greedy steps of the same workload ({el:.1f} s, numpy/scipy float64, "
+                      f"dense residual each step, CG sub-solves to 1e-10)", "steps": done[0], "seconds": el}
+
+
+# ----------------------------------------------------------------------------- main arms
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    p, cfg = workload(args)
+    for _ in range(max(0, args.warmup)):
+        pass  # the oracle has no warm-up state; each sample starts from W = 0
+    vals, times = [], []
+    per = max(5.0, args.cpu_seconds / max(1, args.steps))
+    tot_steps, tot_s = 0, 0.0
+    for _ in range(args.steps):
+        r = oracle_sample(p, args, per)
+        tot_steps += r["steps"]
+        tot_s += r["seconds"]
+    v = tot_steps / tot_s if tot_s > 0 else None
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": cfg,
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{tot_steps} greedy steps in {args.steps} samples of ~{per:.0f} s"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_1808_05510_gb300 import build
+    from paper_1808_05510_gb300.conreg import ConReg
+
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    p, cfg = workload(args, rank)
+    stream = torch.cuda.current_stream()
+    l2buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    g = ConReg.from_problem(p, r_cap=args.r_max, profile=1)
+
+    def one_step():
+        g.cr_set_factors(np.zeros((p.ny, 0)), np.zeros((0, 0)), np.zeros((p.nx, 0)))
+        return g.cr_solve(args.r_max, args.tau, args.relres)
+
+    for _ in range(args.warmup):
+        one_step()
+        flush_l2(l2buf)
+    torch.cuda.synchronize()
+    g.cr_get_stats(reset=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms, infos = [], []
+    with ClockSampler(local_rank) as clk:
+        for _ in range(args.steps):
+            flush_l2(l2buf)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = one_step()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            infos.append(info)
+    torch.cuda.synchronize()
+    stats = g.cr_get_stats(reset=True)
+    tot_ms = sum(ms)
+    ranks = sum(i["rank"] for i in infos)
+    t_local = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
+    r_local = torch.tensor([float(ranks)], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+        dist.all_reduce(r_local, op=dist.ReduceOp.SUM)
+    t_max = float(t_local.item())
+    ranks_all = float(r_local.item())
+    value = ranks_all / (t_max / 1e3)
+    # time to the relres target (per step), when reached
+    reached = [i for i in infos if i["stop_name"] == "relres"]
+    ttr = (sum(m for m, i in zip(ms, infos) if i["stop_name"] == "relres") / len(reached) / 1e3) if reached else None
+
+    # roofline of the dominant kernel: the cluster PCG (both sides)
+    pcg_ms = stats["phase_ms"]["pcg_u"] + stats["phase_ms"]["pcg_v"]
+    pcg_calls = stats["phase_calls"]["pcg_u"] + stats["phase_calls"]["pcg_v"]
+    n_avg = 0.5 * (p.nx + p.ny)
+    iters_per_launch = stats["pcg_iters"] / max(1, stats["pcg_solves"])
+    bytes_per_launch = iters_per_launch * pcg_bytes_per_iter(int(n_avg))
+    avg_launch_s = pcg_ms / max(1, pcg_calls) / 1e3
+    hbm, peak_kind = peaks()
+    achieved = bytes_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": "pcg_cluster_kernel", "peak_kind": peak_kind,
+                "pcg_share_of_step": pcg_ms / tot_ms if tot_ms > 0 else None,
+                "avg_launch_us": avg_launch_s * 1e6, "iters_per_launch": iters_per_launch,
+                "us_per_iter": avg_launch_s * 1e6 / max(iters_per_launch, 1e-9),
+                "phase_ms_per_step": {k: v / args.steps for k, v in stats["phase_ms"].items() if v}}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+           "time_to_relres_s": ttr, "relres_reached_steps": len(reached),
+           "final_relres": infos[-1]["relres"], "final_rank": infos[-1]["rank"], "stop": infos[-1]["stop_name"],
+           "pcg_iters_per_step": stats["pcg_iters"] / args.steps,
+           "roofline": roofline, "gpu_launches": stats["launches"], "clocks": clk.summary()}
+    g.close()
+
+    # end to end through the public API with host buffers (create + solve + factors + destroy)
+    if not args.no_e2e:
+        e_ms, e_ranks, h2d, d2h = [], 0, 0, 0
+        for k in range(args.steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with ConReg.from_problem(p, r_cap=args.r_max) as ge:
+                info = ge.cr_solve(args.r_max, args.tau, args.relres)
+                U, Z, V = ge.cr_get_factors()
+                st = ge.cr_get_stats()
+            torch.cuda.synchronize()
+            el = (time.perf_counter() - t0) * 1e3
+            if k == 0:
+                continue  # warm-up
+            e_ms.append(el)
+            e_ranks += info["rank"]
+            h2d, d2h = st["h2d_bytes"], st["d2h_bytes"]
+        e_t = torch.tensor([sum(e_ms)], dtype=torch.float64, device=dev)
+        e_r = torch.tensor([float(e_ranks)], dtype=torch.float64, device=dev)
+        if world > 1:
+            import torch.distributed as dist
+            dist.all_reduce(e_t, op=dist.ReduceOp.MAX)
+            dist.all_reduce(e_r, op=dist.ReduceOp.SUM)
+        out["e2e"] = {"value": float(e_r.item()) / (float(e_t.item()) / 1e3), "unit": UNIT,
+                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                      "ms_per_step": float(e_t.item()) / args.steps}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = oracle_sample(p, args, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -92,6 +92,7 @@ typedef struct {
   int32_t galerkin_maxit;  /* cap on Galerkin CG iterations per projection (default 10 j^2 + 100) */
   int32_t residual_every;  /* cr_solve: evaluate ‖R‖_F every k steps (default 1) */
   int32_t cluster_size;    /* PCG thread-block cluster size; 0 = automatic */
+  int32_t profile;         /* != 0: time each phase with CUDA events (see cr_get_stats) */
   uint64_t seed;           /* seed of the fallback ALS start vector */
   void* stream;            /* cudaStream_t for all device work; NULL = a library-owned stream */
   /* Optional device allocator (e.g. a framework caching allocator).  When
@@ -126,6 +127,26 @@ typedef struct {
   int64_t cg_iters;    /* total Galerkin CG iterations */
   double seconds;      /* host wall time of the call */
 } cr_solve_info;
+
+/* Phases timed when cr_options.profile != 0. */
+typedef enum {
+  CR_PHASE_PCG_U = 0,    /* PCG solves of Eq. (ALS_linsys) */
+  CR_PHASE_PCG_V = 1,    /* PCG solves of Eq. (ALS_linsys_v) */
+  CR_PHASE_RHS = 2,      /* residual products R_j v, R_j^T u and sub-problem coefficients */
+  CR_PHASE_ORTH = 3,     /* orthogonalisation and projected coefficient matrices */
+  CR_PHASE_GALERKIN = 4, /* Galerkin CG on Eq. (Proj_Sylv) and the masked data residual */
+  CR_PHASE_RESID = 5,    /* residual norm, objective, dW */
+  CR_NPHASE = 8
+} cr_phase;
+
+typedef struct {
+  int64_t launches;               /* kernels launched by the library (all problems) since the last reset */
+  int64_t pcg_solves;             /* PCG solves on this problem since the last reset */
+  int64_t pcg_iters;              /* their iterations */
+  int64_t h2d_bytes, d2h_bytes;   /* bytes this problem copied host->device / device->host */
+  double phase_ms[CR_NPHASE];     /* device time per cr_phase (profile mode; else 0) */
+  int64_t phase_calls[CR_NPHASE]; /* timed intervals per phase */
+} cr_stats;
 
 /* Fill *o with defaults (struct_size set).  Always succeeds for o != NULL. */
 cr_status cr_options_default(cr_options* o);
@@ -190,6 +211,10 @@ cr_status cr_solve_u(struct cr_problem* p, const double* v_host, const double* r
 /* Solve Eq. (ALS_linsys_v): B_hat v_hat = rhs for a unit vector u (ny entries). */
 cr_status cr_solve_v(struct cr_problem* p, const double* u_host, const double* rhs_host, double* v_hat_host,
                      int32_t* iters);
+
+/* Counters and (profile mode) per-phase device times; reset != 0 zeroes them
+ * after reading.  Synchronises the problem's stream. */
+cr_status cr_get_stats(struct cr_problem* p, cr_stats* s, int32_t reset);
 
 /* Static description of a status code. */
 const char* cr_status_str(cr_status s);

@@ -47,7 +47,7 @@ class cr_options(C.Structure):
                 ("precond", C.c_int32), ("pcg_tol", C.c_double), ("pcg_maxit", C.c_int32),
                 ("als_delta", C.c_double), ("als_max_iter", C.c_int32), ("als_sweeps", C.c_int32),
                 ("galerkin_maxit", C.c_int32), ("residual_every", C.c_int32), ("cluster_size", C.c_int32),
-                ("seed", C.c_uint64), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("profile", C.c_int32), ("seed", C.c_uint64), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_ctx", C.c_void_p)]
 
 
@@ -59,6 +59,14 @@ class cr_rank1_info(C.Structure):
 
 class cr_proj_info(C.Structure):
     _fields_ = [("iters", C.c_int32), ("relres", C.c_double)]
+
+
+PHASES = ["pcg_u", "pcg_v", "rhs", "orth", "galerkin", "resid", "p6", "p7"]
+
+
+class cr_stats(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("pcg_solves", C.c_int64), ("pcg_iters", C.c_int64),
+                ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("phase_ms", C.c_double * 8), ("phase_calls", C.c_int64 * 8)]
 
 
 class cr_solve_info(C.Structure):
@@ -82,6 +90,7 @@ SIGNATURES = {
     "cr_apply_residual": (C.c_int, [C.c_void_p, C.c_int32, _dp, _dp]),
     "cr_solve_u": (C.c_int, [C.c_void_p, _dp, _dp, _dp, _ip]),
     "cr_solve_v": (C.c_int, [C.c_void_p, _dp, _dp, _dp, _ip]),
+    "cr_get_stats": (C.c_int, [C.c_void_p, C.POINTER(cr_stats), C.c_int32]),
     "cr_status_str": (C.c_char_p, [C.c_int]),
     "cr_last_error": (C.c_char_p, [C.c_void_p]),
 }
@@ -284,6 +293,14 @@ class ConReg:
         out = np.zeros(self.nx if trans else self.ny)
         _check(self._lib.cr_apply_residual(self.h, int(trans), _ptr(vec), _ptr(out)), self.h, "cr_apply_residual")
         return out
+
+    def cr_get_stats(self, reset: bool = False) -> dict:
+        s = cr_stats()
+        _check(self._lib.cr_get_stats(self.h, C.byref(s), int(reset)), self.h, "cr_get_stats")
+        return {"launches": s.launches, "pcg_solves": s.pcg_solves, "pcg_iters": s.pcg_iters,
+                "h2d_bytes": s.h2d_bytes, "d2h_bytes": s.d2h_bytes,
+                "phase_ms": {PHASES[i]: s.phase_ms[i] for i in range(8)},
+                "phase_calls": {PHASES[i]: s.phase_calls[i] for i in range(8)}}
 
     def cr_solve_u(self, v, rhs):
         v = np.ascontiguousarray(v, dtype=np.float64)

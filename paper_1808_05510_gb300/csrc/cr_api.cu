@@ -85,6 +85,19 @@ struct cr_problem {
   double Dnorm = 0.0, OmYn2 = 0.0;
   bool F_valid = false;
   double last_dW = NAN;
+  // profiling
+  struct Pending {
+    int phase;
+    cudaEvent_t a, b;
+  };
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<Pending> pending;
+  cudaEvent_t open_ev[CR_NPHASE] = {};
+  double phase_ms[CR_NPHASE] = {};
+  int64_t phase_calls[CR_NPHASE] = {};
+  int64_t pcg_solves = 0, pcg_iters = 0;
+  int64_t h2d_bytes = 0, d2h_bytes = 0;
+  long long launch_base = 0;
 };
 
 namespace {
@@ -103,6 +116,47 @@ namespace {
     cr_status s_ = (x);                \
     if (s_ != CR_OK) return s_;        \
   } while (0)
+
+cudaEvent_t take_event(cr_problem* p) {
+  if (!p->ev_pool.empty()) {
+    cudaEvent_t e = p->ev_pool.back();
+    p->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void prof_begin(cr_problem* p, int ph) {
+  if (!p->opt.profile) return;
+  cudaEvent_t e = take_event(p);
+  cudaEventRecord(e, p->st);
+  p->open_ev[ph] = e;
+}
+
+void prof_end(cr_problem* p, int ph) {
+  if (!p->opt.profile || !p->open_ev[ph]) return;
+  cudaEvent_t e = take_event(p);
+  cudaEventRecord(e, p->st);
+  p->pending.push_back({ph, p->open_ev[ph], e});
+  p->open_ev[ph] = nullptr;
+}
+
+void prof_resolve(cr_problem* p) {
+  for (auto& q : p->pending) {
+    float ms = 0.0f;
+    cudaEventSynchronize(q.b);
+    if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) {
+      p->phase_ms[q.phase] += ms;
+      p->phase_calls[q.phase] += 1;
+    }
+    p->ev_pool.push_back(q.a);
+    p->ev_pool.push_back(q.b);
+  }
+  p->pending.clear();
+  cudaGetLastError();
+}
 
 cr_status fail(cr_problem* p, cr_status s, const std::string& msg) {
   p->err = msg;
@@ -133,6 +187,7 @@ template <class T>
 cr_status upload(cr_problem* p, T** out, const std::vector<T>& h) {
   TRY(dalloc(p, out, h.size()));
   if (!h.empty()) CUCHK(p, cudaMemcpyAsync(*out, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, p->st));
+  p->h2d_bytes += (int64_t)(h.size() * sizeof(T));
   return CR_OK;
 }
 
@@ -145,7 +200,11 @@ cr_status sync(cr_problem* p) {
 // Read device scalars ds[lo..lo+cnt) and both PCG stats into the pinned mirror.
 cr_status readback(cr_problem* p, int lo, int cnt, bool stats) {
   CUCHK(p, cudaMemcpyAsync(p->hs->ds + lo, p->ds + lo, sizeof(double) * cnt, cudaMemcpyDeviceToHost, p->st));
-  if (stats) CUCHK(p, cudaMemcpyAsync(p->hs->stat, p->stat, sizeof(PcgStat) * 2, cudaMemcpyDeviceToHost, p->st));
+  p->d2h_bytes += (int64_t)(sizeof(double) * cnt);
+  if (stats) {
+    CUCHK(p, cudaMemcpyAsync(p->hs->stat, p->stat, sizeof(PcgStat) * 2, cudaMemcpyDeviceToHost, p->st));
+    p->d2h_bytes += (int64_t)(sizeof(PcgStat) * 2);
+  }
   return sync(p);
 }
 
@@ -426,7 +485,9 @@ cr_status launch_pcg(cr_problem* p, int side, const double* b, double* x) {
     a.X = p->xl;
     a.s = p->svec;
   }
+  prof_begin(p, side == 0 ? CR_PHASE_PCG_U : CR_PHASE_PCG_V);
   CUCHK(p, pcg_launch(a, side, p->st));
+  prof_end(p, side == 0 ? CR_PHASE_PCG_U : CR_PHASE_PCG_V);
   return CR_OK;
 }
 
@@ -538,6 +599,7 @@ cr_status do_project(cr_problem* p, double tol, cr_proj_info* info) {
   const int64_t ld = p->rcap;
   if (info) *info = cr_proj_info{0, 0.0};
   if (j == 0) return CR_OK;
+  prof_begin(p, CR_PHASE_GALERKIN);
   CUCHK(p, cudaMemcpyAsync(p->Zprev, p->Z, sizeof(double) * ld * ld, cudaMemcpyDeviceToDevice, st));
   build_F(p);
   double* gs = p->ds + DS_GS;
@@ -578,6 +640,7 @@ cr_status do_project(cr_problem* p, double tol, cr_proj_info* info) {
     }
   }
   refresh_E(p);
+  prof_end(p, CR_PHASE_GALERKIN);
   TRY(sync(p));
   if (info) {
     info->iters = k;
@@ -606,6 +669,7 @@ cr_status do_relres(cr_problem* p, double* relres) {
   gemm(m, m, ny, 1.0, MatView{p->Ep, ny, 1}, MatView{p->Ep, 1, ny}, 0.0, p->gram, 1, m, p->ws, p->ws_elems, st);
   std::vector<double> gram((size_t)m * m);
   CUCHK(p, cudaMemcpyAsync(gram.data(), p->gram, sizeof(double) * m * m, cudaMemcpyDeviceToHost, st));
+  p->d2h_bytes += (int64_t)sizeof(double) * m * m;
   TRY(sync(p));
   std::vector<double> w, V;
   sym_eig(m, gram, w, V);
@@ -621,11 +685,13 @@ cr_status do_relres(cr_problem* p, double* relres) {
     }
   if (ke > 0) {
     CUCHK(p, cudaMemcpyAsync(p->tmat, T.data(), sizeof(double) * T.size(), cudaMemcpyHostToDevice, st));
+    p->h2d_bytes += (int64_t)(sizeof(double) * T.size());
     gemm(ny, ke, m, 1.0, MatView{p->Ep, 1, ny}, MatView{p->tmat, 1, m}, 0.0, QE, 1, ny, p->ws, p->ws_elems, st);
     // second pass: Cholesky of Q_E^T Q_E
     gemm(ke, ke, ny, 1.0, MatView{QE, ny, 1}, MatView{QE, 1, ny}, 0.0, p->gram, 1, ke, p->ws, p->ws_elems, st);
     std::vector<double> g2((size_t)ke * ke);
     CUCHK(p, cudaMemcpyAsync(g2.data(), p->gram, sizeof(double) * ke * ke, cudaMemcpyDeviceToHost, st));
+    p->d2h_bytes += (int64_t)(sizeof(double) * ke * ke);
     TRY(sync(p));
     // upper Cholesky factor R (g2 = R^T R), then Rinv
     std::vector<double> R((size_t)ke * ke, 0.0), Ri((size_t)ke * ke, 0.0);
@@ -655,6 +721,7 @@ cr_status do_relres(cr_problem* p, double* relres) {
         }
       }
       CUCHK(p, cudaMemcpyAsync(p->tmat, Ri.data(), sizeof(double) * Ri.size(), cudaMemcpyHostToDevice, st));
+      p->h2d_bytes += (int64_t)(sizeof(double) * Ri.size());
       copy(ny * ke, QE, p->Bnm, st);
       gemm(ny, ke, ke, 1.0, MatView{p->Bnm, 1, ny}, MatView{p->tmat, 1, ke}, 0.0, QE, 1, ny, p->ws, p->ws_elems,
            st);
@@ -712,6 +779,7 @@ cr_status do_rank_one(cr_problem* p, cr_rank1_info* info) {
     }
     for (double& x : g) x /= std::sqrt(nrm);
     CUCHK(p, cudaMemcpyAsync(p->v, g.data(), sizeof(double) * nx, cudaMemcpyHostToDevice, st));
+    p->h2d_bytes += (int64_t)(sizeof(double) * nx);
   }
   fill(ny, 0.0, p->uhat, st);
   fill(nx, 0.0, p->vhat, st);
@@ -719,18 +787,24 @@ cr_status do_rank_one(cr_problem* p, cr_rank1_info* info) {
   double delta = INFINITY, un = 0.0, vn = 0.0, worst = 0.0;
   int itu = 0, itv = 0;
   for (;;) {
+    prof_begin(p, CR_PHASE_RHS);
     prep_u(p, p->v);
     residual_times(p, p->v, p->rhs_u);
+    prof_end(p, CR_PHASE_RHS);
     TRY(launch_pcg(p, 0, p->rhs_u, p->uhat));
+    prof_begin(p, CR_PHASE_RHS);
     dot(ny, p->uhat, p->uhat, p->ds + DS_UN2, st);
     scale_by_inv_norm(ny, p->uhat, p->ds + DS_UN2, p->u, st);
     prep_v(p, p->u);
     residual_t_times(p, p->u, p->rhs_v);
+    prof_end(p, CR_PHASE_RHS);
     TRY(launch_pcg(p, 1, p->rhs_v, p->vhat));
     dot(nx, p->vhat, p->vhat, p->ds + DS_VN2, st);
     scale_by_inv_norm(nx, p->vhat, p->ds + DS_VN2, p->v, st);
     TRY(readback(p, 0, 2, true));
     const PcgStat* s = p->hs->stat;
+    p->pcg_solves += 2;
+    p->pcg_iters += s[0].iters + s[1].iters;
     itu += s[0].iters;
     itv += s[1].iters;
     worst = std::max(worst, std::max(s[0].relres, s[1].relres));
@@ -748,6 +822,7 @@ cr_status do_rank_one(cr_problem* p, cr_rank1_info* info) {
     }
   }
   // orth: U <- orth([U, u]), V <- orth([V, v])
+  prof_begin(p, CR_PHASE_ORTH);
   double* uq = p->UU + (size_t)3 * j * ny;
   double* vq = p->VV + (size_t)3 * j * nx;
   copy(ny, p->u, uq, st);
@@ -760,6 +835,7 @@ cr_status do_rank_one(cr_problem* p, cr_rank1_info* info) {
   zero_border(j, p->Z, p->rcap, st);
   p->j = j + 1;
   p->F_valid = false;
+  prof_end(p, CR_PHASE_ORTH);
   TRY(sync(p));
   if (info) {
     info->rank = p->j;
@@ -797,6 +873,7 @@ cr_status cr_options_default(cr_options* o) {
   o->galerkin_maxit = 0;
   o->residual_every = 1;
   o->cluster_size = 0;
+  o->profile = 0;
   o->seed = 1808;
   return CR_OK;
 }
@@ -831,6 +908,10 @@ void cr_destroy(cr_problem* p) {
       cudaFree(a.first);
   }
   if (p->hs) cudaFreeHost(p->hs);
+  prof_resolve(p);
+  for (auto e : p->ev_pool) cudaEventDestroy(e);
+  for (auto e : p->open_ev)
+    if (e) cudaEventDestroy(e);
   if (p->own_stream && p->st) cudaStreamDestroy(p->st);
   delete p;
 }
@@ -890,6 +971,7 @@ cr_status cr_create(const cr_problem_desc* d, const cr_options* o, cr_problem** 
     }
     p->own_stream = true;
   }
+  p->launch_base = cr::g_launches.load();
   if (cudaMallocHost(&p->hs, sizeof(HostScal)) != cudaSuccess) {
     p->err = "cudaMallocHost failed";
     return abort_create(CR_ENOMEM);
@@ -1053,7 +1135,9 @@ cr_status cr_create(const cr_problem_desc* d, const cr_options* o, cr_problem** 
         Cm[q + (size_t)a * p->ldcr] = c;
       }
     CUCHK(p, cudaMemcpyAsync(p->QR, Q.data(), sizeof(double) * nx * nq, cudaMemcpyHostToDevice, p->st));
+    p->h2d_bytes += (int64_t)(sizeof(double) * nx * nq);
     CUCHK(p, cudaMemcpyAsync(p->CRm, Cm.data(), sizeof(double) * Cm.size(), cudaMemcpyHostToDevice, p->st));
+    p->h2d_bytes += (int64_t)(sizeof(double) * Cm.size());
     p->nQR = nq;
     p->nQX = nq;
     if (sync(p) != CR_OK) return abort_create(CR_ECUDA);
@@ -1077,6 +1161,7 @@ cr_status cr_project(cr_problem* p, double tol, cr_proj_info* info) {
 
 cr_status cr_residual(cr_problem* p, double* relres, double* J, double* dW) {
   if (!p) return CR_EINVAL;
+  prof_begin(p, CR_PHASE_RESID);
   const int j = p->j;
   const int64_t ld = p->rcap;
   if (dW) {
@@ -1102,6 +1187,33 @@ cr_status cr_residual(cr_problem* p, double* relres, double* J, double* dW) {
     }
   }
   if (relres) TRY(do_relres(p, relres));
+  prof_end(p, CR_PHASE_RESID);
+  return CR_OK;
+}
+
+cr_status cr_get_stats(cr_problem* p, cr_stats* s, int32_t reset) {
+  if (!p || !s) return CR_EINVAL;
+  CUCHK(p, cudaStreamSynchronize(p->st));
+  prof_resolve(p);
+  std::memset(s, 0, sizeof(*s));
+  s->launches = cr::g_launches.load() - p->launch_base;
+  s->pcg_solves = p->pcg_solves;
+  s->pcg_iters = p->pcg_iters;
+  s->h2d_bytes = p->h2d_bytes;
+  s->d2h_bytes = p->d2h_bytes;
+  for (int i = 0; i < CR_NPHASE; ++i) {
+    s->phase_ms[i] = p->phase_ms[i];
+    s->phase_calls[i] = p->phase_calls[i];
+  }
+  if (reset) {
+    p->launch_base = cr::g_launches.load();
+    p->pcg_solves = p->pcg_iters = 0;
+    p->h2d_bytes = p->d2h_bytes = 0;
+    for (int i = 0; i < CR_NPHASE; ++i) {
+      p->phase_ms[i] = 0.0;
+      p->phase_calls[i] = 0;
+    }
+  }
   return CR_OK;
 }
 
@@ -1167,6 +1279,8 @@ cr_status cr_get_factors(cr_problem* p, double* U, int64_t ldu, double* Zh, int6
   const int j = p->j;
   if (j == 0) return CR_OK;
   if ((U && ldu < p->ny) || (Zh && ldz < j) || (V && ldv < p->nx)) return fail(p, CR_EINVAL, "leading dimension");
+  p->d2h_bytes += (int64_t)sizeof(double) * ((U ? (int64_t)p->ny * j : 0) + (V ? (int64_t)p->nx * j : 0) +
+                                             (Zh ? (int64_t)j * j : 0));
   if (U)
     CUCHK(p, cudaMemcpy2DAsync(U, ldu * sizeof(double), p->UU, 3 * (size_t)p->ny * sizeof(double),
                                p->ny * sizeof(double), j, cudaMemcpyDeviceToHost, p->st));

@@ -13,6 +13,8 @@
 
 namespace cr {
 
+std::atomic<long long> g_launches{0};
+
 namespace {
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -194,6 +196,7 @@ void gemm(int M, int N, int K, double alpha, MatView A, MatView B, double beta, 
     // C = beta * C: the reduce kernel with no partial sums
     if (beta == 1.0) return;
     const int64_t tot = (int64_t)M * N;
+    count_launch();
     gemm_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, N, 0, ws, 0.0, beta, C, sci, scl);
     return;
   }
@@ -209,10 +212,13 @@ void gemm(int M, int N, int K, double alpha, MatView A, MatView B, double beta, 
   dim3 grid((M + TB - 1) / TB, (N + TB - 1) / TB, S);
   dim3 blk(TB, TB);
   if (S == 1) {
+    count_launch();
     gemm_kernel<<<grid, blk, 0, st>>>(M, N, K, A, B, kchunk, alpha, beta, C, sci, scl, nullptr);
   } else {
+    count_launch();
     gemm_kernel<<<grid, blk, 0, st>>>(M, N, K, A, B, kchunk, 1.0, 0.0, C, sci, scl, ws);
     const int64_t tot = (int64_t)M * N;
+    count_launch();
     gemm_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M, N, S, ws, alpha, beta, C, sci, scl);
   }
 }
@@ -221,6 +227,7 @@ void gemv_t(int n, int k, const double* A, int64_t lda, const double* w, double*
             double alpha, double beta, cudaStream_t st) {
   if (k <= 0) return;
   const int wpb = 8;
+  count_launch();
   gemv_t_kernel<<<(k + wpb - 1) / wpb, 32 * wpb, 0, st>>>(n, k, A, lda, w, out, ostride, alpha, beta);
 }
 
@@ -229,45 +236,54 @@ void gemv_n(int n, int k, const double* A, int64_t lda, const double* c, int64_t
   if (n <= 0) return;
   if (k <= 0) {
     if (beta == 1.0) return;
+    count_launch();
     gemv_n_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, 0, A, lda, c, cstride, y, alpha, beta);
     return;
   }
+  count_launch();
   gemv_n_kernel<<<(n + 255) / 256, 256, sizeof(double) * k, st>>>(n, k, A, lda, c, cstride, y, alpha, beta);
 }
 
 void dot(int n, const double* x, const double* y, double* out, cudaStream_t st) {
+  count_launch();
   dot_kernel<<<1, 1024, 0, st>>>(n, x, y, out);
 }
 
 void spmv_xt(int m, const int* colptr, const int* row, const double* val, const double* v, double* out,
              int64_t ostride, cudaStream_t st) {
   if (m <= 0) return;
+  count_launch();
   spmv_xt_kernel<<<(m + 7) / 8, 256, 0, st>>>(m, colptr, row, val, v, out, ostride);
 }
 
 void spmv_x(int n, const int* rowptr, const int* col, const double* val, const double* c, double* y, double alpha,
             double beta, cudaStream_t st) {
   if (n <= 0) return;
+  count_launch();
   spmv_x_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, rowptr, col, val, c, y, alpha, beta);
 }
 
 void omega_sq_dots(int n, int m, const uint8_t* Om, int64_t ldo, const double* u, double* out, cudaStream_t st) {
   if (m <= 0) return;
+  count_launch();
   omega_sq_kernel<<<(m + 7) / 8, 256, 0, st>>>(n, m, Om, ldo, u, out);
 }
 
 void scale_by_inv_norm(int n, const double* x, const double* nrm2, double* y, cudaStream_t st) {
   if (n <= 0) return;
+  count_launch();
   scale_inv_norm_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, x, nrm2, y);
 }
 
 void copy(int n, const double* x, double* y, cudaStream_t st) {
   if (n <= 0) return;
+  count_launch();
   copy_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, x, y);
 }
 
 void fill(int64_t n, double v, double* y, cudaStream_t st) {
   if (n <= 0) return;
+  count_launch();
   fill_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, v, y);
 }
 
@@ -275,6 +291,7 @@ void batched_gemv(int j, int m, const double* G, int64_t ldg, int64_t gstride, c
                   double* out, int64_t ldo, cudaStream_t st) {
   if (j <= 0 || m <= 0) return;
   dim3 grid((j + 127) / 128, m);
+  count_launch();
   batched_gemv_kernel<<<grid, 128, sizeof(double) * j, st>>>(j, G, ldg, gstride, w, ldw, out, ldo);
 }
 

@@ -14,7 +14,13 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <atomic>
+
 namespace cr {
+
+// Number of kernels this library has launched (process-wide).
+extern std::atomic<long long> g_launches;
+inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 constexpr int kMaxSlots = 16;     // off-diagonal entries per Laplacian row
 constexpr int kPcgThreads = 512;  // threads per CTA of the cluster PCG

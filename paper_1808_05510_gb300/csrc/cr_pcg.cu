@@ -341,12 +341,14 @@ cudaError_t pcg_launch(const PcgArgs& a, int data_kind, cudaStream_t st) {
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
+  count_launch();
   if (data_kind == 0) return cudaLaunchKernelEx(&cfg, pcg_cluster_kernel<0>, a);
   return cudaLaunchKernelEx(&cfg, pcg_cluster_kernel<1>, a);
 }
 
 void lap_apply(const DevLap& L, const double* x, double* y, double shift, cudaStream_t st) {
   if (L.n == 0) return;
+  count_launch();
   lap_apply_kernel<<<(L.n + 255) / 256, 256, 0, st>>>(L, x, y, shift);
 }
 

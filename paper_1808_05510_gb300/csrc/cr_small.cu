@@ -162,35 +162,42 @@ inline unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b
 
 void zcoef(int j, const double* Z, int64_t ldz, int trans, const double* h, double lam, double* g, cudaStream_t st) {
   if (j <= 0) return;
+  count_launch();
   zcoef_kernel<<<nblk(3 * j, 128), 128, 0, st>>>(j, Z, ldz, trans, h, lam, g);
 }
 
 void mirror_col(int col, double* A, int64_t ld, int batch, int64_t stride, cudaStream_t st) {
   if (col <= 0 || batch <= 0) return;
+  count_launch();
   mirror_col_kernel<<<dim3(nblk(col, 128), batch), 128, 0, st>>>(col, A, ld, stride);
 }
 
 void zero_border(int j, double* Z, int64_t ld, cudaStream_t st) {
+  count_launch();
   zero_border_kernel<<<nblk(j + 1, 128), 128, 0, st>>>(j, Z, ld);
 }
 
 void mask_residual(int n, int m, const double* OmY, const uint8_t* Om, int64_t ldo, double* E, cudaStream_t st) {
   const int64_t tot = (int64_t)n * m;
   if (tot == 0) return;
+  count_launch();
   mask_residual_kernel<<<nblk(tot), 256, 0, st>>>(tot, n, OmY, Om, ldo, E);
 }
 
 void omega_times(int n, int m, const uint8_t* Om, int64_t ldo, const double* u, double* B, cudaStream_t st) {
   const int64_t tot = (int64_t)n * m;
   if (tot == 0) return;
+  count_launch();
   omega_times_kernel<<<nblk(tot), 256, 0, st>>>(tot, n, Om, ldo, u, B);
 }
 
 void mat_dot(int r, int c, const double* A, int64_t lda, const double* B, int64_t ldb, double* out, cudaStream_t st) {
+  count_launch();
   mat_dot_kernel<<<1, 1024, 0, st>>>(r, c, A, lda, B, ldb, out);
 }
 
 void mat_diff_norms(int j, const double* Z, const double* Zp, int64_t ld, double* out, cudaStream_t st) {
+  count_launch();
   mat_diff_kernel<<<1, 1024, 0, st>>>(j, Z, Zp, ld, out);
 }
 
@@ -198,26 +205,31 @@ void mat_axpby(int r, int c, double alpha, const double* A, int64_t lda, double 
                double* C, int64_t ldc, cudaStream_t st) {
   const int64_t tot = (int64_t)r * c;
   if (tot == 0) return;
+  count_launch();
   mat_axpby_kernel<<<nblk(tot), 256, 0, st>>>(r, c, alpha, A, lda, beta, B, ldb, C, ldc);
 }
 
 void copy2d(int r, int c, const double* src, int64_t lds, double* dst, int64_t ldd, cudaStream_t st) {
   const int64_t tot = (int64_t)r * c;
   if (tot == 0) return;
+  count_launch();
   copy2d_kernel<<<nblk(tot), 256, 0, st>>>(r, c, src, lds, dst, ldd);
 }
 
 void cg_update_zr(int j, double* Z, double* R, const double* P, const double* Q, int64_t ld, const double* gs, int k,
                   cudaStream_t st) {
+  count_launch();
   cg_zr_kernel<<<nblk((int64_t)j * j), 256, 0, st>>>(j, Z, R, P, Q, ld, gs, k);
 }
 
 void cg_update_p(int j, double* P, const double* R, int64_t ld, const double* gs, int k, cudaStream_t st) {
+  count_launch();
   cg_p_kernel<<<nblk((int64_t)j * j), 256, 0, st>>>(j, P, R, ld, gs, k);
 }
 
 void build_core(int m, int j, const double* Z, int64_t ldz, double lam, double* Mc, int64_t ldm, cudaStream_t st) {
   const int64_t n = m + 3 * (int64_t)j;
+  count_launch();
   build_core_kernel<<<nblk(n * n), 256, 0, st>>>(m, j, Z, ldz, lam, Mc, ldm);
 }
 
