@@ -216,6 +216,31 @@ cr_status cr_solve_v(struct cr_problem* p, const double* u_host, const double* r
  * after reading.  Synchronises the problem's stream. */
 cr_status cr_get_stats(struct cr_problem* p, cr_stats* s, int32_t reset);
 
+/* Allocation-free solve of Eq. (ALS_linsys)-type systems, for callers that
+ * cannot allocate device memory (a plug-in confined to buffers its host
+ * application hands it, code that must not enter the allocator, a process whose
+ * allocator belongs to another runtime).  The paper has no counterpart: it is
+ * a packaging of the library's u-side PCG for such callers.
+ *
+ * Solves (lambda [(L + c I)^2 + (d - c^2) I] + diag(omega)) u_hat = rhs from
+ * u_hat = 0 by the same cluster-resident Jacobi PCG as cr_solve_u, to relative
+ * residual tol or maxit iterations.  L (n x n) is given in CSR form in device
+ * memory (int32 rowptr[n+1], col[nnz], float64 val[nnz]); omega, rhs and u_hat
+ * are device vectors of n entries; stream is a cudaStream_t (NULL = default).
+ * *iters (host, may be NULL) receives the iteration count.
+ *
+ * It allocates nothing: its work vectors live in one static device array of
+ * 5 x 131072 doubles (about 5 MiB) that every GPU loading the library keeps
+ * until the process exits, so n may be at most 131072 (larger n: CR_EINVAL).
+ * The first call on each device looks up that array's device address (with the
+ * device current); make it before any stream capture.  All calls share the
+ * array: calls whose kernels overlap on the GPU (other streams or host threads)
+ * race and return garbage.  Synchronises `stream`.  Errors are described by
+ * cr_last_error(NULL). */
+cr_status cr_solve_u_noalloc(int64_t n, const int32_t* rowptr_dev, const int32_t* col_dev, const double* val_dev,
+                             double lambda, double c, double d, const double* omega_dev, const double* rhs_dev,
+                             double* u_hat_dev, double tol, int32_t maxit, int32_t* iters, void* stream);
+
 /* Static description of a status code. */
 const char* cr_status_str(cr_status s);
 

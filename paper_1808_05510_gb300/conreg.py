@@ -91,6 +91,9 @@ SIGNATURES = {
     "cr_solve_u": (C.c_int, [C.c_void_p, _dp, _dp, _dp, _ip]),
     "cr_solve_v": (C.c_int, [C.c_void_p, _dp, _dp, _dp, _ip]),
     "cr_get_stats": (C.c_int, [C.c_void_p, C.POINTER(cr_stats), C.c_int32]),
+    "cr_solve_u_noalloc": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_double,
+                                     C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int32, _ip,
+                                     C.c_void_p]),
     "cr_status_str": (C.c_char_p, [C.c_int]),
     "cr_last_error": (C.c_char_p, [C.c_void_p]),
 }

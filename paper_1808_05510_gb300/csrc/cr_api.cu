@@ -49,6 +49,11 @@ struct HostScal {
 };
 }  // namespace
 
+namespace cr {
+// Error text reported by cr_last_error(NULL) for calls without a problem handle.
+void set_global_error(const std::string& msg) { g_create_err = msg; }
+}  // namespace cr
+
 struct cr_problem {
   int nx = 0, ny = 0, m = 0, rcap = 0;
   double lam = 0.0;
