@@ -268,6 +268,7 @@ def run_ours(args, rank, world, local_rank):
            "time_to_relres_s": ttr, "relres_reached_steps": len(reached),
            "final_relres": infos[-1]["relres"], "final_rank": infos[-1]["rank"], "stop": infos[-1]["stop_name"],
            "pcg_iters_per_step": stats["pcg_iters"] / args.steps,
+           "galerkin_cg_iters_per_step": sum(i["cg_iters"] for i in infos) / args.steps,
            "roofline": roofline, "gpu_launches": stats["launches"], "clocks": clk.summary()}
     g.close()
 

@@ -80,7 +80,7 @@ struct cr_problem {
   double* ds = nullptr;
   HostScal* hs = nullptr;  // pinned
   double *gR = nullptr, *gP = nullptr, *gQ = nullptr, *gZB2 = nullptr, *gZB1 = nullptr, *gZH = nullptr,
-         *gGw = nullptr;
+         *gGw = nullptr, *gDg = nullptr, *gT = nullptr;
   double *QL = nullptr, *CL = nullptr, *QR = nullptr, *CRm = nullptr, *Cx = nullptr, *Cx2 = nullptr, *Ep = nullptr,
          *CE = nullptr, *CP = nullptr, *Mc = nullptr, *T1 = nullptr, *T2 = nullptr, *gram = nullptr, *tmat = nullptr;
   int nQL = 0, nQR = 0, nQX = 0;
@@ -478,6 +478,7 @@ cr_status launch_pcg(cr_problem* p, int side, const double* b, double* x) {
   a.tol = p->opt.pcg_tol;
   a.maxit = p->opt.pcg_maxit;
   a.stat = p->stat + side;
+  a.force_generic = p->opt.pcg_kernel == 1;
   if (side == 0) {
     a.L = p->Ly;
     a.coef = p->coef + 0;
@@ -598,6 +599,12 @@ cr_status grow_projections(cr_problem* p, int q) {
   return grow_bases(p, q);
 }
 
+// Galerkin projection (Eq. Proj_Sylv) by matrix-valued CG from the current Z
+// (the previous Z padded with zeros: the warm start of Sec. 2.3), stopped when
+// ||F - K(Z)||_F <= tol ||F||_F.  The CG is preconditioned with the diagonal of
+// K (the paper's CG is unpreconditioned; the iterate it converges to is the
+// same Galerkin solution).  Device scalars: gs[k & 1] = <R_k, D^-1 R_k>,
+// gs[2] = <P, K P>, gs[3] = |F|^2, gs[4] = |R|^2.
 cr_status do_project(cr_problem* p, double tol, cr_proj_info* info) {
   cudaStream_t st = p->st;
   const int j = p->j;
@@ -608,32 +615,32 @@ cr_status do_project(cr_problem* p, double tol, cr_proj_info* info) {
   CUCHK(p, cudaMemcpyAsync(p->Zprev, p->Z, sizeof(double) * ld * ld, cudaMemcpyDeviceToDevice, st));
   build_F(p);
   double* gs = p->ds + DS_GS;
+  galerkin_diag(j, p->m, p->A1, p->A2, p->B1, p->B2, p->G, p->H, ld, p->lam, p->gDg, st);
   galerkin_apply(p, p->Z, p->gQ);
   mat_axpby(j, j, 1.0, p->F, ld, -1.0, p->gQ, ld, p->gR, ld, st);  // R = F - K(Z)
-  copy2d(j, j, p->gR, ld, p->gP, ld, st);
-  mat_dot(j, j, p->gR, ld, p->gR, ld, gs + 0, st);
+  precond_dots(j, p->gR, p->gDg, ld, p->gP, gs + 0, gs + 4, st);   // P = D^-1 R
   mat_dot(j, j, p->F, ld, p->F, ld, gs + 3, st);
-  TRY(readback(p, DS_GS, 4, false));
+  TRY(readback(p, DS_GS, 5, false));
   const double fn2 = p->hs->ds[DS_GS + 3];
-  double rho = p->hs->ds[DS_GS + 0];
+  double rr = p->hs->ds[DS_GS + 4];
   const double thr2 = tol * tol * fn2;
   const int maxit = p->opt.galerkin_maxit > 0 ? p->opt.galerkin_maxit : 10 * j * j + 100;
   int k = 0;
   cr_status rc = CR_OK;
-  if (fn2 > 0.0 && rho > thr2) {
+  if (fn2 > 0.0 && rr > thr2) {
     for (;;) {
       galerkin_apply(p, p->gP, p->gQ);
       mat_dot(j, j, p->gP, ld, p->gQ, ld, gs + 2, st);
       cg_update_zr(j, p->Z, p->gR, p->gP, p->gQ, ld, gs, k, st);
-      mat_dot(j, j, p->gR, ld, p->gR, ld, gs + ((k + 1) & 1), st);
-      cg_update_p(j, p->gP, p->gR, ld, gs, k, st);
+      precond_dots(j, p->gR, p->gDg, ld, p->gT, gs + ((k + 1) & 1), gs + 4, st);
+      cg_update_p(j, p->gP, p->gT, ld, gs, k, st);
       ++k;
       const bool check = k < 8 || (k % 4) == 0 || k >= maxit;
       if (check) {
-        TRY(readback(p, DS_GS, 3, false));
-        rho = p->hs->ds[DS_GS + (k & 1)];
-        if (!(rho > thr2)) break;
-        if (!std::isfinite(rho)) {
+        TRY(readback(p, DS_GS, 5, false));
+        rr = p->hs->ds[DS_GS + 4];
+        if (!(rr > thr2)) break;
+        if (!std::isfinite(rr)) {
           rc = fail(p, CR_ENOTCONV, "Galerkin CG produced a non-finite residual");
           break;
         }
@@ -649,7 +656,7 @@ cr_status do_project(cr_problem* p, double tol, cr_proj_info* info) {
   TRY(sync(p));
   if (info) {
     info->iters = k;
-    info->relres = fn2 > 0.0 ? std::sqrt(std::max(rho, 0.0) / fn2) : 0.0;
+    info->relres = fn2 > 0.0 ? std::sqrt(std::max(rr, 0.0) / fn2) : 0.0;
   }
   return rc;
 }
@@ -879,6 +886,7 @@ cr_status cr_options_default(cr_options* o) {
   o->residual_every = 1;
   o->cluster_size = 0;
   o->profile = 0;
+  o->pcg_kernel = 0;
   o->seed = 1808;
   return CR_OK;
 }
@@ -1070,7 +1078,7 @@ cr_status cr_create(const cr_problem_desc* d, const cr_options* o, cr_problem** 
   CK(dalloc(p, &p->UU, (size_t)3 * rc * ny));
   CK(dalloc(p, &p->VV, (size_t)3 * rc * nx));
   for (double** b : {&p->Z, &p->Zprev, &p->A1, &p->A2, &p->B1, &p->B2, &p->F, &p->gR, &p->gP, &p->gQ, &p->gZB2,
-                     &p->gZB1})
+                     &p->gZB1, &p->gDg, &p->gT})
     CK(dalloc(p, b, r2));
   for (double** b : {&p->H, &p->P, &p->Mzh, &p->gZH, &p->gGw}) CK(dalloc(p, b, (size_t)rc * m));
   CK(dalloc(p, &p->G, r2 * m));

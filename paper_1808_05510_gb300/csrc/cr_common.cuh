@@ -89,6 +89,7 @@ struct PcgArgs {
   double tol;
   int maxit;
   PcgStat* stat;           // device
+  int force_generic;       // 1: always use the shared/global-memory kernel
 };
 
 // ---------------------------------------------------------------- cr_pcg.cu
@@ -170,4 +171,10 @@ void cg_update_p(int j, double* P, const double* R, int64_t ld, const double* gs
 // columns, and for the factor block (3p+s, 3q+t): -lam Z(p,q) for (s,t)=(0,2),
 // -2 lam Z(p,q) for (1,1), -lam Z(p,q) for (2,0).
 void build_core(int m, int j, const double* Z, int64_t ldz, double lam, double* Mc, int64_t ldm, cudaStream_t st);
+// Dg(p, q) = diagonal of the projected operator at Z(p, q) (Jacobi preconditioner of the Galerkin CG)
+void galerkin_diag(int j, int m, const double* A1, const double* A2, const double* B1, const double* B2,
+                   const double* G, const double* H, int64_t ld, double lam, double* Dg, cudaStream_t st);
+// Zp = R ./ Dg, out0 = <R, Zp>, out1 = <R, R>
+void precond_dots(int j, const double* R, const double* Dg, int64_t ld, double* Zp, double* out0, double* out1,
+                  cudaStream_t st);
 }  // namespace cr

@@ -268,6 +268,288 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_cluster_kernel(const PcgAr
   }
 }
 
+// ---------------------------------------------------------------------------
+// Register-resident variant for unit-weight Laplacians with at most 6
+// neighbours per row and at most VPT rows per thread: every per-row quantity
+// (x, r, p, s, Jacobi and data diagonals, the 6 neighbour addresses) stays in
+// registers for the whole solve, neighbours are read with one
+// ld.shared::cluster each from addresses resolved once with mapa (a missing
+// neighbour points at a zero word), and the iteration scalars are formed once
+// per CTA by one thread.  Same Chronopoulos-Gear recurrence and reduction
+// order as pcg_cluster_kernel.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t mapa_u32(uint32_t a, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ double ld_dsm(uint32_t a) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
+  return v;
+}
+
+constexpr int kRegSlots = 6;
+
+template <int KIND, int VPT>
+__global__ void __launch_bounds__(kPcgThreads, 1) pcg_reg_kernel(const PcgArgs A) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const DevLap& L = A.L;
+  const int chunk = L.chunk;
+  const int beg = rank * chunk;
+  const int nloc = max(0, min(L.n - beg, chunk));
+  const int m = A.m;
+  extern __shared__ __align__(16) double sm[];
+  // layout: [zero word pad 2] [ub0 chunk] [ub1 chunk] [tb chunk] [red 8] [ypart m] [sS m] [sY m] [scr 128] [scal 8]
+  double* zero = sm;
+  double* ub0 = sm + 2;
+  double* ub1 = ub0 + chunk;
+  double* tb = ub1 + chunk;
+  double* red = tb + chunk;
+  double* ypart = red + 8;
+  double* sS = ypart + m;
+  double* sY = sS + m;
+  double* scr = sY + m;
+  double* scal = scr + 128;
+  const uint32_t off_ub1 = (uint32_t)(chunk * sizeof(double));
+  const uint32_t off_tb = (uint32_t)(2 * chunk * sizeof(double));
+  const double lam = A.lam;
+  const double c = A.coef[0];
+  const double d = A.coef[1];
+  const double e = d - c * c;
+  if (threadIdx.x == 0) {
+    zero[0] = 0.0;
+    zero[1] = 0.0;
+  }
+  for (int a = threadIdx.x; a < m; a += blockDim.x) sS[a] = KIND == 0 ? A.xi[a] * A.xi[a] : A.s[a];
+  __syncthreads();
+
+  double x[VPT], r[VPT], p[VPT], sv[VPT], dpc[VPT], dinv[VPT], omt[VPT];
+  uint32_t na[VPT][kRegSlots];
+  int xr0[VPT], xr1[VPT];
+  bool own[VPT];
+  const uint32_t zaddr = mapa_u32(smem_u32(zero), (uint32_t)rank);
+  const uint32_t base0 = smem_u32(ub0);
+#pragma unroll
+  for (int k = 0; k < VPT; ++k) {
+    const int li = threadIdx.x + k * blockDim.x;
+    own[k] = li < nloc;
+    const int i = beg + (own[k] ? li : 0);
+    x[k] = r[k] = p[k] = sv[k] = 0.0;
+    dpc[k] = dinv[k] = omt[k] = 0.0;
+    xr0[k] = xr1[k] = 0;
+#pragma unroll
+    for (int q = 0; q < kRegSlots; ++q) na[k][q] = zaddr;
+    if (own[k]) {
+#pragma unroll
+      for (int q = 0; q < kRegSlots; ++q) {
+        if (q < L.K) {
+          const int pk = L.nbrp[(size_t)q * L.n + i];
+          // a missing neighbour reads the zero word (offset cancelled by subtracting the buffer offsets below)
+          if (pk >= 0) na[k][q] = mapa_u32(base0 + (uint32_t)((pk & 0xFFFFFF) * sizeof(double)), (uint32_t)(pk >> 24));
+        }
+      }
+      dpc[k] = L.diag[i] + c;
+      double dd = lam * (L.l2diag[i] + 2.0 * c * L.diag[i] + d);
+      if (KIND == 0) {
+        double o = 0.0;
+        for (int a = 0; a < m; ++a) o += (double)A.Om[i + (int64_t)a * A.ldo] * sS[a];
+        omt[k] = o;
+        dd += o;
+      } else {
+        xr0[k] = A.X.xr_ptr[i];
+        xr1[k] = A.X.xr_ptr[i + 1];
+        for (int q = xr0[k]; q < xr1[k]; ++q) dd += A.X.xr_val[q] * A.X.xr_val[q] * sS[A.X.xr_col[q]];
+      }
+      dinv[k] = dd > 0.0 ? 1.0 / dd : 1.0;
+      x[k] = A.x[i];
+    }
+  }
+
+  // neighbour sum of the buffer at byte offset `off` from ub0 (zero word for a missing neighbour)
+  auto nsum = [&](int k, uint32_t off) -> double {
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < kRegSlots; ++q) {
+      const uint32_t a = na[k][q];
+      acc += ld_dsm(a == zaddr ? a : a + off);
+    }
+    return acc;
+  };
+  // v side: partial X^T of the buffer in shared memory
+  auto ypartial = [&](double* buf) {
+    if (KIND == 1) {
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+      for (int a = wid; a < m; a += nw) {
+        const int p0 = A.X.lx_ptr[rank * m + a], p1 = A.X.lx_ptr[rank * m + a + 1];
+        double acc = 0.0;
+        for (int q = p0 + lane; q < p1; q += 32) acc += A.X.lx_val[q] * buf[A.X.lx_row[q]];
+        acc = warp_sum(acc);
+        if (lane == 0) ypart[a] = acc;
+      }
+    }
+  };
+  auto gather = [&]() {
+    if (KIND == 1) {
+      for (int a = threadIdx.x; a < m; a += blockDim.x) {
+        double t = 0.0;
+        for (int rr = 0; rr < C; ++rr) t += cl.map_shared_rank(ypart, (unsigned)rr)[a];
+        sY[a] = sS[a] * t;
+      }
+      __syncthreads();
+    }
+  };
+  auto data = [&](int k, double ui) -> double {
+    if (KIND == 0) return omt[k] * ui;
+    double acc = 0.0;
+    for (int q = xr0[k]; q < xr1[k]; ++q) acc += A.X.xr_val[q] * sY[A.X.xr_col[q]];
+    return acc;
+  };
+
+  // r0 = b - A x0
+  double tt[VPT];
+#pragma unroll
+  for (int k = 0; k < VPT; ++k)
+    if (own[k]) ub0[threadIdx.x + k * blockDim.x] = x[k];
+  cl.sync();
+#pragma unroll
+  for (int k = 0; k < VPT; ++k) {
+    tt[k] = own[k] ? dpc[k] * x[k] - nsum(k, 0) : 0.0;
+    if (own[k]) tb[threadIdx.x + k * blockDim.x] = tt[k];
+  }
+  ypartial(ub0);
+  cl.sync();
+  gather();
+  {
+    double v[1] = {0.0};
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) {
+      if (!own[k]) continue;
+      const int i = beg + threadIdx.x + k * blockDim.x;
+      const double wi = lam * (dpc[k] * tt[k] - nsum(k, off_tb) + e * x[k]) + data(k, x[k]);
+      const double bi = A.b[i];
+      r[k] = bi - wi;
+      v[0] += bi * bi;
+    }
+    block_sum<1>(v, scr, red);
+  }
+  cl.sync();
+  cluster_sum<1>(cl, red, scal, C);
+  const double bb = scal[0];
+  int it = 0, status = 0;
+  double rho = 0.0;
+  if (bb > 0.0) {
+    const double tol2 = A.tol * A.tol * bb;
+    double gam_prev = 1.0, alpha_prev = 1.0;  // used by thread 0 only
+    int cur = 1;
+    for (;;) {
+      const uint32_t off_ub = cur ? off_ub1 : 0u;
+      double* ub = cur ? ub1 : ub0;
+      double u[VPT];
+#pragma unroll
+      for (int k = 0; k < VPT; ++k) {
+        u[k] = r[k] * dinv[k];
+        if (own[k]) ub[threadIdx.x + k * blockDim.x] = u[k];
+      }
+      cl.sync();
+#pragma unroll
+      for (int k = 0; k < VPT; ++k) {
+        tt[k] = own[k] ? dpc[k] * u[k] - nsum(k, off_ub) : 0.0;
+        if (own[k]) tb[threadIdx.x + k * blockDim.x] = tt[k];
+      }
+      ypartial(ub);
+      cl.sync();
+      gather();
+      double v[3] = {0.0, 0.0, 0.0};
+      double w[VPT];
+#pragma unroll
+      for (int k = 0; k < VPT; ++k) {
+        w[k] = own[k] ? lam * (dpc[k] * tt[k] - nsum(k, off_tb) + e * u[k]) + data(k, u[k]) : 0.0;
+        v[0] += r[k] * u[k];
+        v[1] += u[k] * w[k];
+        v[2] += r[k] * r[k];
+      }
+      block_sum<3>(v, scr, red);
+      cl.sync();
+      // cross-CTA sums and the recurrence scalars, formed once per CTA
+      if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        double g = 0.0, dl = 0.0, rh = 0.0;
+        if (lane < C) {
+          const double* rr = cl.map_shared_rank(red, lane);
+          g = rr[0];
+          dl = rr[1];
+          rh = rr[2];
+        }
+        g = warp_sum(g);
+        dl = warp_sum(dl);
+        rh = warp_sum(rh);
+        if (lane == 0) {
+          double flag = 0.0, alpha = 0.0, beta = 0.0;
+          if (rh <= tol2) {
+            flag = 1.0;
+          } else if (it >= A.maxit) {
+            flag = 2.0;
+          } else {
+            double den = dl;
+            if (it > 0) {
+              beta = g / gam_prev;
+              den = dl - beta * g / alpha_prev;
+            }
+            if (!(den > 0.0) || !isfinite(den)) {
+              flag = 3.0;
+            } else {
+              alpha = g / den;
+              gam_prev = g;
+              alpha_prev = alpha;
+            }
+          }
+          scal[0] = flag;
+          scal[1] = alpha;
+          scal[2] = beta;
+          scal[3] = rh;
+        }
+      }
+      __syncthreads();
+      const double flag = scal[0];
+      rho = scal[3];
+      if (flag == 1.0) break;
+      if (flag == 2.0) {
+        status = 1;
+        break;
+      }
+      if (flag == 3.0) {
+        status = 2;
+        break;
+      }
+      const double alpha = scal[1], beta = scal[2];
+#pragma unroll
+      for (int k = 0; k < VPT; ++k) {
+        p[k] = it == 0 ? u[k] : u[k] + beta * p[k];
+        sv[k] = it == 0 ? w[k] : w[k] + beta * sv[k];
+        x[k] += alpha * p[k];
+        r[k] -= alpha * sv[k];
+      }
+      cur ^= 1;
+      ++it;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < VPT; ++k)
+    if (own[k]) A.x[beg + threadIdx.x + k * blockDim.x] = x[k];
+  cl.sync();  // no CTA leaves while another can still read its shared memory
+  if (rank == 0 && threadIdx.x == 0) {
+    A.stat->iters = it;
+    A.stat->status = status;
+    A.stat->relres = bb > 0.0 ? sqrt(rho / bb) : 0.0;
+    A.stat->bnorm = sqrt(bb);
+  }
+}
+
 __global__ void lap_apply_kernel(const DevLap L, const double* __restrict__ x, double* __restrict__ y,
                                  double shift) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -283,14 +565,25 @@ __global__ void lap_apply_kernel(const DevLap L, const double* __restrict__ x, d
 
 }  // namespace
 
-size_t pcg_smem_bytes(int chunk, int m) { return sizeof(double) * (3 * (size_t)chunk + 8 + 3 * (size_t)m + 128 + 8); }
+size_t pcg_smem_bytes(int chunk, int m) { return sizeof(double) * (3 * (size_t)chunk + 8 + 3 * (size_t)m + 128 + 8 + 2); }
+
+// Register-resident variant usable for this operator?  Returns VPT (0 = no).
+int pcg_reg_vpt(const DevLap& L) {
+  if (L.offw != nullptr || L.K > kRegSlots) return 0;
+  if (L.chunk <= kPcgThreads) return 1;
+  if (L.chunk <= 2 * kPcgThreads) return 2;
+  return 0;
+}
 
 cudaError_t pcg_prepare(int /*data_kind*/, int csize, size_t /*smem_bytes*/) {
   // the attribute is per kernel, shared by the x and y grids: allow the maximum
   const size_t smem_bytes = 227 * 1024;
   cudaError_t e;
-  for (int kind = 0; kind < 2; ++kind) {
-    const void* fn = kind == 0 ? (const void*)pcg_cluster_kernel<0> : (const void*)pcg_cluster_kernel<1>;
+  const void* fns[6] = {(const void*)pcg_cluster_kernel<0>, (const void*)pcg_cluster_kernel<1>,
+                        (const void*)pcg_reg_kernel<0, 1>,  (const void*)pcg_reg_kernel<1, 1>,
+                        (const void*)pcg_reg_kernel<0, 2>,  (const void*)pcg_reg_kernel<1, 2>};
+  for (int kind = 0; kind < 6; ++kind) {
+    const void* fn = fns[kind];
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     if (e != cudaSuccess) return e;
     if (csize > 8) {
@@ -342,6 +635,15 @@ cudaError_t pcg_launch(const PcgArgs& a, int data_kind, cudaStream_t st) {
   cfg.attrs = at;
   cfg.numAttrs = 1;
   count_launch();
+  const int vpt = a.force_generic ? 0 : pcg_reg_vpt(a.L);
+  if (vpt == 1) {
+    if (data_kind == 0) return cudaLaunchKernelEx(&cfg, pcg_reg_kernel<0, 1>, a);
+    return cudaLaunchKernelEx(&cfg, pcg_reg_kernel<1, 1>, a);
+  }
+  if (vpt == 2) {
+    if (data_kind == 0) return cudaLaunchKernelEx(&cfg, pcg_reg_kernel<0, 2>, a);
+    return cudaLaunchKernelEx(&cfg, pcg_reg_kernel<1, 2>, a);
+  }
   if (data_kind == 0) return cudaLaunchKernelEx(&cfg, pcg_cluster_kernel<0>, a);
   return cudaLaunchKernelEx(&cfg, pcg_cluster_kernel<1>, a);
 }

@@ -234,3 +234,81 @@ void build_core(int m, int j, const double* Z, int64_t ldz, double lam, double* 
 }
 
 }  // namespace cr
+
+namespace cr {
+namespace {
+
+// Diagonal of the projected operator of Eq. (Proj_Sylv) acting on Z(p, q):
+//   lam (B2_qq + 2 A1_pp B1_qq + A2_pp) + sum_a G_a,pp H_qa^2
+__global__ void galerkin_diag_kernel(int j, int m, const double* __restrict__ A1, const double* __restrict__ A2,
+                                     const double* __restrict__ B1, const double* __restrict__ B2,
+                                     const double* __restrict__ G, const double* __restrict__ H, int64_t ld,
+                                     double lam, double* __restrict__ Dg) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)j * j) return;
+  const int pp = (int)(t % j), q = (int)(t / j);
+  double v = lam * (B2[q + q * ld] + 2.0 * A1[pp + pp * ld] * B1[q + q * ld] + A2[pp + pp * ld]);
+  for (int a = 0; a < m; ++a) {
+    const double h = H[q + (int64_t)a * ld];
+    v = fma(G[(int64_t)a * ld * ld + pp + pp * ld] * h, h, v);
+  }
+  Dg[pp + q * ld] = v > 0.0 ? v : 1.0;
+}
+
+// Zp = R ./ Dg; out[0] = <R, Zp>, out[1] = <R, R> (one block, fixed order)
+__global__ void precond_dots_kernel(int j, const double* __restrict__ R, const double* __restrict__ Dg, int64_t ld,
+                                    double* __restrict__ Zp, double* out0, double* out1) {
+  __shared__ double scr[64];
+  double a = 0.0, b = 0.0;
+  const int64_t tot = (int64_t)j * j;
+  for (int64_t t = threadIdx.x; t < tot; t += blockDim.x) {
+    const int64_t o = (t % j) + (t / j) * ld;
+    const double r = R[o];
+    const double z = r / Dg[o];
+    Zp[o] = z;
+    a = fma(r, z, a);
+    b = fma(r, r, b);
+  }
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, s);
+    b += __shfl_down_sync(0xffffffffu, b, s);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) {
+    scr[wid] = a;
+    scr[32 + wid] = b;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    a = lane < nw ? scr[lane] : 0.0;
+    b = lane < nw ? scr[32 + lane] : 0.0;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, s);
+      b += __shfl_down_sync(0xffffffffu, b, s);
+    }
+    if (lane == 0) {
+      *out0 = a;
+      *out1 = b;
+    }
+  }
+}
+
+}  // namespace
+
+void galerkin_diag(int j, int m, const double* A1, const double* A2, const double* B1, const double* B2,
+                   const double* G, const double* H, int64_t ld, double lam, double* Dg, cudaStream_t st) {
+  const int64_t tot = (int64_t)j * j;
+  if (tot == 0) return;
+  count_launch();
+  galerkin_diag_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(j, m, A1, A2, B1, B2, G, H, ld, lam, Dg);
+}
+
+void precond_dots(int j, const double* R, const double* Dg, int64_t ld, double* Zp, double* out0, double* out1,
+                  cudaStream_t st) {
+  count_launch();
+  precond_dots_kernel<<<1, 1024, 0, st>>>(j, R, Dg, ld, Zp, out0, out1);
+}
+
+}  // namespace cr

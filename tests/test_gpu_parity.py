@@ -84,14 +84,15 @@ def test_residual_products_set_state(cr, prob):
         assert np.array_equal(Ug, U) and np.array_equal(Zg, Z) and np.array_equal(Vg, V)
 
 
-def test_als_subsolves(cr, prob):
+@pytest.mark.parametrize("kernel", [0, 1], ids=["auto", "generic"])
+def test_als_subsolves(cr, prob, kernel):
     p, o = prob
     rng = np.random.default_rng(4)
     v = synth.random_unit(p.nx, 5)
     u = synth.random_unit(p.ny, 6)
     rhs_u = rng.standard_normal(p.ny)
     rhs_v = rng.standard_normal(p.nx)
-    with cr.ConReg.from_problem(p, r_cap=4, pcg_tol=1e-13, pcg_maxit=50000) as g:
+    with cr.ConReg.from_problem(p, r_cap=4, pcg_tol=1e-13, pcg_maxit=50000, pcg_kernel=kernel) as g:
         uh, itu = g.cr_solve_u(v, rhs_u)
         vh, itv = g.cr_solve_v(u, rhs_v)
     assert itu > 0 and itv > 0
@@ -120,11 +121,12 @@ def test_galerkin_projection_and_residual(cr, prob):
     assert abs(res["dW"] - dWo) <= 1e-10 * dWo
 
 
-def test_greedy_trajectory(cr, prob):
+@pytest.mark.parametrize("kernel", [0, 1], ids=["auto", "generic"])
+def test_greedy_trajectory(cr, prob, kernel):
     p, o = prob
     r = min(8, p.nx - 1)
     steps = []
-    with cr.ConReg.from_problem(p, r_cap=r, pcg_tol=1e-13, pcg_maxit=50000, als_sweeps=2) as g:
+    with cr.ConReg.from_problem(p, r_cap=r, pcg_tol=1e-13, pcg_maxit=50000, als_sweeps=2, pcg_kernel=kernel) as g:
         for _ in range(r):
             g.cr_add_rank_one()
             g.cr_project(1e-13)
