@@ -94,6 +94,7 @@ typedef struct {
   int32_t cluster_size;    /* PCG thread-block cluster size; 0 = automatic */
   int32_t profile;         /* != 0: time each phase with CUDA events (see cr_get_stats) */
   int32_t pcg_kernel;      /* 0 = automatic (register-resident kernel when it applies), 1 = generic kernel */
+  int32_t galerkin_kernel; /* 0 = one persistent cooperative launch per projection, 1 = one launch per step */
   uint64_t seed;           /* seed of the fallback ALS start vector */
   void* stream;            /* cudaStream_t for all device work; NULL = a library-owned stream */
   /* Optional device allocator (e.g. a framework caching allocator).  When

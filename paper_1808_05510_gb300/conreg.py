@@ -47,7 +47,8 @@ class cr_options(C.Structure):
                 ("precond", C.c_int32), ("pcg_tol", C.c_double), ("pcg_maxit", C.c_int32),
                 ("als_delta", C.c_double), ("als_max_iter", C.c_int32), ("als_sweeps", C.c_int32),
                 ("galerkin_maxit", C.c_int32), ("residual_every", C.c_int32), ("cluster_size", C.c_int32),
-                ("profile", C.c_int32), ("pcg_kernel", C.c_int32), ("seed", C.c_uint64), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("profile", C.c_int32), ("pcg_kernel", C.c_int32), ("galerkin_kernel", C.c_int32),
+                ("seed", C.c_uint64), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_ctx", C.c_void_p)]
 
 

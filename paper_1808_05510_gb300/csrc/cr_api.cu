@@ -80,7 +80,10 @@ struct cr_problem {
   double* ds = nullptr;
   HostScal* hs = nullptr;  // pinned
   double *gR = nullptr, *gP = nullptr, *gQ = nullptr, *gZB2 = nullptr, *gZB1 = nullptr, *gZH = nullptr,
-         *gGw = nullptr, *gDg = nullptr, *gT = nullptr;
+         *gGw = nullptr, *gDg = nullptr, *gT = nullptr, *gzb = nullptr, *gpart = nullptr, *gout = nullptr;
+  unsigned* gbar = nullptr;
+  int* gerr = nullptr;
+  int gal_nb = 0;
   double *QL = nullptr, *CL = nullptr, *QR = nullptr, *CRm = nullptr, *Cx = nullptr, *Cx2 = nullptr, *Ep = nullptr,
          *CE = nullptr, *CP = nullptr, *Mc = nullptr, *T1 = nullptr, *T2 = nullptr, *gram = nullptr, *tmat = nullptr;
   int nQL = 0, nQR = 0, nQX = 0;
@@ -616,38 +619,62 @@ cr_status do_project(cr_problem* p, double tol, cr_proj_info* info) {
   build_F(p);
   double* gs = p->ds + DS_GS;
   galerkin_diag(j, p->m, p->A1, p->A2, p->B1, p->B2, p->G, p->H, ld, p->lam, p->gDg, st);
-  galerkin_apply(p, p->Z, p->gQ);
-  mat_axpby(j, j, 1.0, p->F, ld, -1.0, p->gQ, ld, p->gR, ld, st);  // R = F - K(Z)
-  precond_dots(j, p->gR, p->gDg, ld, p->gP, gs + 0, gs + 4, st);   // P = D^-1 R
-  mat_dot(j, j, p->F, ld, p->F, ld, gs + 3, st);
-  TRY(readback(p, DS_GS, 5, false));
-  const double fn2 = p->hs->ds[DS_GS + 3];
-  double rr = p->hs->ds[DS_GS + 4];
-  const double thr2 = tol * tol * fn2;
   const int maxit = p->opt.galerkin_maxit > 0 ? p->opt.galerkin_maxit : 10 * j * j + 100;
   int k = 0;
+  double fn2 = 0.0, rr = 0.0;
   cr_status rc = CR_OK;
-  if (fn2 > 0.0 && rr > thr2) {
-    for (;;) {
-      galerkin_apply(p, p->gP, p->gQ);
-      mat_dot(j, j, p->gP, ld, p->gQ, ld, gs + 2, st);
-      cg_update_zr(j, p->Z, p->gR, p->gP, p->gQ, ld, gs, k, st);
-      precond_dots(j, p->gR, p->gDg, ld, p->gT, gs + ((k + 1) & 1), gs + 4, st);
-      cg_update_p(j, p->gP, p->gT, ld, gs, k, st);
-      ++k;
-      const bool check = k < 8 || (k % 4) == 0 || k >= maxit;
-      if (check) {
-        TRY(readback(p, DS_GS, 5, false));
-        rr = p->hs->ds[DS_GS + 4];
-        if (!(rr > thr2)) break;
-        if (!std::isfinite(rr)) {
-          rc = fail(p, CR_ENOTCONV, "Galerkin CG produced a non-finite residual");
+  if (p->opt.galerkin_kernel == 0 && p->gal_nb > 0) {
+    // one cooperative launch runs the whole CG
+    mat_dot(j, j, p->F, ld, p->F, ld, gs + 3, st);
+    TRY(readback(p, DS_GS + 3, 1, false));
+    fn2 = p->hs->ds[DS_GS + 3];
+    if (fn2 > 0.0) {
+      CUCHK(p, cudaMemsetAsync(p->gbar, 0, 2 * sizeof(unsigned), st));
+      CUCHK(p, cudaMemsetAsync(p->gerr, 0, sizeof(int), st));
+      CUCHK(p, galerkin_cg_launch(p->gal_nb, j, p->m, ld, p->lam, p->A1, p->A2, p->B1, p->B2, p->G, p->H, p->F,
+                                  p->gDg, p->Z, p->gR, p->gP, p->gT, p->gQ, p->gZB2, p->gZB1, p->gZH, p->gGw, p->gzb,
+                                  p->gpart, p->gbar, p->gerr, tol * tol * fn2, maxit, p->gout, st));
+      double out[3] = {0, 0, 0};
+      CUCHK(p, cudaMemcpyAsync(out, p->gout, sizeof(out), cudaMemcpyDeviceToHost, st));
+      p->d2h_bytes += (int64_t)sizeof(out);
+      TRY(sync(p));
+      k = (int)out[0];
+      rr = out[1];
+      if (out[2] == 1.0) rc = fail(p, CR_ENOTCONV, "Galerkin CG reached its iteration cap");
+      if (out[2] == 2.0) rc = fail(p, CR_ENOTCONV, "Galerkin CG broke down (non-positive curvature)");
+      if (out[2] == 3.0) return fail(p, CR_ETIMEOUT, "Galerkin CG grid barrier timed out");
+    }
+  } else {
+    galerkin_apply(p, p->Z, p->gQ);
+    mat_axpby(j, j, 1.0, p->F, ld, -1.0, p->gQ, ld, p->gR, ld, st);  // R = F - K(Z)
+    precond_dots(j, p->gR, p->gDg, ld, p->gP, gs + 0, gs + 4, st);   // P = D^-1 R
+    mat_dot(j, j, p->F, ld, p->F, ld, gs + 3, st);
+    TRY(readback(p, DS_GS, 5, false));
+    fn2 = p->hs->ds[DS_GS + 3];
+    rr = p->hs->ds[DS_GS + 4];
+    const double thr2 = tol * tol * fn2;
+    if (fn2 > 0.0 && rr > thr2) {
+      for (;;) {
+        galerkin_apply(p, p->gP, p->gQ);
+        mat_dot(j, j, p->gP, ld, p->gQ, ld, gs + 2, st);
+        cg_update_zr(j, p->Z, p->gR, p->gP, p->gQ, ld, gs, k, st);
+        precond_dots(j, p->gR, p->gDg, ld, p->gT, gs + ((k + 1) & 1), gs + 4, st);
+        cg_update_p(j, p->gP, p->gT, ld, gs, k, st);
+        ++k;
+        const bool check = k < 8 || (k % 4) == 0 || k >= maxit;
+        if (check) {
+          TRY(readback(p, DS_GS, 5, false));
+          rr = p->hs->ds[DS_GS + 4];
+          if (!(rr > thr2)) break;
+          if (!std::isfinite(rr)) {
+            rc = fail(p, CR_ENOTCONV, "Galerkin CG produced a non-finite residual");
+            break;
+          }
+        }
+        if (k >= maxit) {
+          rc = fail(p, CR_ENOTCONV, "Galerkin CG reached its iteration cap");
           break;
         }
-      }
-      if (k >= maxit) {
-        rc = fail(p, CR_ENOTCONV, "Galerkin CG reached its iteration cap");
-        break;
       }
     }
   }
@@ -887,6 +914,7 @@ cr_status cr_options_default(cr_options* o) {
   o->cluster_size = 0;
   o->profile = 0;
   o->pcg_kernel = 0;
+  o->galerkin_kernel = 0;
   o->seed = 1808;
   return CR_OK;
 }
@@ -1078,7 +1106,7 @@ cr_status cr_create(const cr_problem_desc* d, const cr_options* o, cr_problem** 
   CK(dalloc(p, &p->UU, (size_t)3 * rc * ny));
   CK(dalloc(p, &p->VV, (size_t)3 * rc * nx));
   for (double** b : {&p->Z, &p->Zprev, &p->A1, &p->A2, &p->B1, &p->B2, &p->F, &p->gR, &p->gP, &p->gQ, &p->gZB2,
-                     &p->gZB1, &p->gDg, &p->gT})
+                     &p->gZB1, &p->gDg, &p->gT, &p->gzb})
     CK(dalloc(p, b, r2));
   for (double** b : {&p->H, &p->P, &p->Mzh, &p->gZH, &p->gGw}) CK(dalloc(p, b, (size_t)rc * m));
   CK(dalloc(p, &p->G, r2 * m));
@@ -1093,6 +1121,11 @@ cr_status cr_create(const cr_problem_desc* d, const cr_options* o, cr_problem** 
   CK(dalloc(p, &p->gc, (size_t)3 * rc + m));
   CK(dalloc(p, &p->cvec, (size_t)3 * rc + 2 * m));
   CK(dalloc(p, &p->coef, 8));
+  p->gal_nb = galerkin_grid_size();
+  CK(dalloc(p, &p->gpart, (size_t)4 * std::max(1, p->gal_nb)));
+  CK(dalloc(p, &p->gout, 4));
+  CK(dalloc(p, &p->gbar, 2));
+  CK(dalloc(p, &p->gerr, 1));
   CK(dalloc(p, &p->stat, 2));
   CK(dalloc(p, &p->ds, DS_COUNT));
   // residual-norm bases and core workspaces

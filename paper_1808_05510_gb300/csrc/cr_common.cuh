@@ -140,6 +140,15 @@ void fill(int64_t n, double v, double* y, cudaStream_t st);
 void batched_gemv(int j, int m, const double* G, int64_t ldg, int64_t gstride, const double* w, int64_t ldw,
                   double* out, int64_t ldo, cudaStream_t st);
 
+// ---------------------------------------------------------------- cr_galerkin.cu
+// CTAs of the persistent Galerkin CG (one per SM), 0 if the kernel cannot run.
+int galerkin_grid_size();
+cudaError_t galerkin_cg_launch(int nb, int j, int m, int64_t ld, double lam, const double* A1, const double* A2,
+                               const double* B1, const double* B2, const double* G, const double* H,
+                               const double* F, const double* Dg, double* Z, double* R, double* Pa, double* Pb,
+                               double* Q, double* T2, double* T1, double* TH, double* Gw, double* zb, double* part,
+                               unsigned* bar, int* err, double tol2, int maxit, double* out, cudaStream_t st);
+
 }  // namespace cr
 
 namespace cr {

@@ -100,12 +100,13 @@ def test_als_subsolves(cr, prob, kernel):
     assert rel(vh, o.solve_v(u, rhs_v)) < 1e-9
 
 
-def test_galerkin_projection_and_residual(cr, prob):
+@pytest.mark.parametrize("gk", [0, 1], ids=["persistent", "launches"])
+def test_galerkin_projection_and_residual(cr, prob, gk):
     p, o = prob
     j = 5
     U, Z0, V = rand_state(o, j, 7)
     Z0 *= 1e-3
-    with cr.ConReg.from_problem(p, r_cap=6) as g:
+    with cr.ConReg.from_problem(p, r_cap=6, galerkin_kernel=gk) as g:
         g.cr_set_factors(U, Z0, V)
         info = g.cr_project(1e-13)
         _, Zg, _ = g.cr_get_factors()
@@ -126,7 +127,8 @@ def test_greedy_trajectory(cr, prob, kernel):
     p, o = prob
     r = min(8, p.nx - 1)
     steps = []
-    with cr.ConReg.from_problem(p, r_cap=r, pcg_tol=1e-13, pcg_maxit=50000, als_sweeps=2, pcg_kernel=kernel) as g:
+    with cr.ConReg.from_problem(p, r_cap=r, pcg_tol=1e-13, pcg_maxit=50000, als_sweeps=2, pcg_kernel=kernel,
+                                galerkin_kernel=kernel) as g:
         for _ in range(r):
             g.cr_add_rank_one()
             g.cr_project(1e-13)
@@ -139,3 +141,22 @@ def test_greedy_trajectory(cr, prob, kernel):
         assert rel(Wg, Wo) < 1e-9
         assert abs(rg["relres"] - so.relres) <= 1e-8 * so.relres
         assert abs(rg["J"] - so.J) <= 1e-9 * abs(so.J)
+
+
+def test_galerkin_kernels_agree_at_larger_rank(cr):
+    """Persistent and per-step Galerkin CG give the same Z at j = 40 (several tiles, ragged edges)."""
+    p = synth.masked3d()
+    o = Oracle.from_problem(p)
+    j = 40
+    U, Z0, V = rand_state(o, j, 9)
+    Z0 *= 1e-4
+    Zs = []
+    for gk in (0, 1):
+        with cr.ConReg.from_problem(p, r_cap=j, galerkin_kernel=gk) as g:
+            g.cr_set_factors(U, Z0, V)
+            g.cr_project(1e-12)
+            Zs.append(g.cr_get_factors()[1])
+    A1, A2, B1, B2, G, Hs, F = o.projected(U, V)
+    resid = np.linalg.norm(F - o.K_apply(Zs[0], A1, A2, B1, B2, G, Hs)) / np.linalg.norm(F)
+    assert resid < 1e-11
+    assert rel(Zs[0], Zs[1]) < 1e-9
