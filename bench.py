@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--r-max", type=int, default=100)
     ap.add_argument("--tau", type=float, default=1e-9)
     ap.add_argument("--relres", type=float, default=1e-6)
-    ap.add_argument("--precision", default="fp64", choices=["fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
+                    help="form reported as the headline value; the float64 form is always measured beside it")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -62,7 +63,7 @@ def workload(args, rank=0):
     cfg = {
         "workload": "visual-cortex-shaped synthetic: smooth random blob mask in a 40^3 box, 7-point Laplacians",
         "ny": p.ny, "nx": p.nx, "ninj": p.m, "lambda": p.lam, "r_max": args.r_max, "tau": args.tau,
-        "relres_target": args.relres, "precision": args.precision,
+        "relres_target": args.relres, "precision": args.precision, "pcg_tol": 1e-10, "pcg_tol_mixed": 1e-6,
         "l2": "flushed between steps (256 MiB write)", "parallelism": "replicas",
     }
     return p, cfg
@@ -127,11 +128,12 @@ def peaks():
         return 6800.0, "of fallback"
 
 
-def pcg_bytes_per_iter(n: int, slots: int = 6) -> float:
-    """Algorithmic bytes of one float64 Chronopoulos-Gear PCG iteration: read and
-    write r, x, p, s (64 B), read the Jacobi diagonal and the data diagonal
-    (16 B), read the neighbour table once (4 B per slot)."""
-    return n * (64.0 + 16.0 + 4.0 * slots)
+def pcg_bytes_per_iter(n: int, slots: int = 6, word: float = 8.0) -> float:
+    """Algorithmic bytes of one Chronopoulos-Gear PCG iteration: read and write
+    r, x, p, s (8 words), read the Jacobi diagonal and the data diagonal (2
+    words), read the neighbour table once (4 B per slot); word = 8 (float64) or
+    4 (float32)."""
+    return n * (10.0 * word + 4.0 * slots)
 
 
 # ----------------------------------------------------------------------------- CPU oracle
@@ -201,76 +203,87 @@ def run_ours(args, rank, world, local_rank):
     p, cfg = workload(args, rank)
     stream = torch.cuda.current_stream()
     l2buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    g = ConReg.from_problem(p, r_cap=args.r_max, profile=1)
+    from paper_1808_05510_gb300.conreg import CR_FP64, CR_MIXED
 
-    def one_step():
-        g.cr_set_factors(np.zeros((p.ny, 0)), np.zeros((0, 0)), np.zeros((p.nx, 0)))
-        return g.cr_solve(args.r_max, args.tau, args.relres)
+    def measure(prec):
+        g = ConReg.from_problem(p, r_cap=args.r_max, profile=1, precision=prec)
 
-    for _ in range(args.warmup):
-        one_step()
-        flush_l2(l2buf)
-    torch.cuda.synchronize()
-    g.cr_get_stats(reset=True)
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    torch.cuda.synchronize()
-    ms, infos = [], []
-    with ClockSampler(local_rank) as clk:
-        for _ in range(args.steps):
+        def one_step():
+            g.cr_set_factors(np.zeros((p.ny, 0)), np.zeros((0, 0)), np.zeros((p.nx, 0)))
+            return g.cr_solve(args.r_max, args.tau, args.relres)
+
+        for _ in range(args.warmup):
+            one_step()
             flush_l2(l2buf)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            info = one_step()
-            e1.record(stream)
-            e1.synchronize()
-            ms.append(e0.elapsed_time(e1))
-            infos.append(info)
-    torch.cuda.synchronize()
-    stats = g.cr_get_stats(reset=True)
-    tot_ms = sum(ms)
-    ranks = sum(i["rank"] for i in infos)
-    t_local = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
-    r_local = torch.tensor([float(ranks)], dtype=torch.float64, device=dev)
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-        dist.all_reduce(r_local, op=dist.ReduceOp.SUM)
-    t_max = float(t_local.item())
-    ranks_all = float(r_local.item())
-    value = ranks_all / (t_max / 1e3)
-    # time to the relres target (per step), when reached
-    reached = [i for i in infos if i["stop_name"] == "relres"]
-    ttr = (sum(m for m, i in zip(ms, infos) if i["stop_name"] == "relres") / len(reached) / 1e3) if reached else None
+        torch.cuda.synchronize()
+        g.cr_get_stats(reset=True)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+        ms, infos = [], []
+        with ClockSampler(local_rank) as clk:
+            for _ in range(args.steps):
+                flush_l2(l2buf)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                info = one_step()
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+                infos.append(info)
+        torch.cuda.synchronize()
+        stats = g.cr_get_stats(reset=True)
+        g.close()
+        tot_ms = sum(ms)
+        ranks = sum(i["rank"] for i in infos)
+        t_local = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
+        r_local = torch.tensor([float(ranks)], dtype=torch.float64, device=dev)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+            dist.all_reduce(r_local, op=dist.ReduceOp.SUM)
+        t_max = float(t_local.item())
+        value = float(r_local.item()) / (t_max / 1e3)
+        reached = [i for i in infos if i["stop_name"] == "relres"]
+        ttr = (sum(m for m, i in zip(ms, infos) if i["stop_name"] == "relres") / len(reached) / 1e3) if reached else None
+        pcg_ms = stats["phase_ms"]["pcg_u"] + stats["phase_ms"]["pcg_v"]
+        pcg_calls = stats["phase_calls"]["pcg_u"] + stats["phase_calls"]["pcg_v"]
+        iters_per_launch = stats["pcg_iters"] / max(1, stats["pcg_solves"])
+        word = 8.0 if prec == CR_FP64 else 4.0
+        bytes_per_launch = iters_per_launch * pcg_bytes_per_iter(int(0.5 * (p.nx + p.ny)), word=word)
+        avg_launch_s = pcg_ms / max(1, pcg_calls) / 1e3
+        achieved = bytes_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
+        return {"value": value, "ms_per_step": t_max / args.steps, "time_to_relres_s": ttr,
+                "relres_reached_steps": len(reached), "final_relres": infos[-1]["relres"],
+                "final_rank": infos[-1]["rank"], "stop": infos[-1]["stop_name"],
+                "pcg_iters_per_step": stats["pcg_iters"] / args.steps,
+                "galerkin_cg_iters_per_step": sum(i["cg_iters"] for i in infos) / args.steps,
+                "phase_ms_per_step": {k: v / args.steps for k, v in stats["phase_ms"].items() if v},
+                "gpu_launches": stats["launches"], "clocks": clk.summary(),
+                "pcg": {"achieved": achieved, "avg_launch_us": avg_launch_s * 1e6, "iters_per_launch": iters_per_launch,
+                        "us_per_iter": avg_launch_s * 1e6 / max(iters_per_launch, 1e-9),
+                        "share_of_step": pcg_ms / tot_ms if tot_ms > 0 else None}}
 
-    # roofline of the dominant kernel: the cluster PCG (both sides)
-    pcg_ms = stats["phase_ms"]["pcg_u"] + stats["phase_ms"]["pcg_v"]
-    pcg_calls = stats["phase_calls"]["pcg_u"] + stats["phase_calls"]["pcg_v"]
-    n_avg = 0.5 * (p.nx + p.ny)
-    iters_per_launch = stats["pcg_iters"] / max(1, stats["pcg_solves"])
-    bytes_per_launch = iters_per_launch * pcg_bytes_per_iter(int(n_avg))
-    avg_launch_s = pcg_ms / max(1, pcg_calls) / 1e3
+    forms = {"fp64": measure(CR_FP64), "mixed": measure(CR_MIXED)}
+    head = forms[args.precision]
     hbm, peak_kind = peaks()
-    achieved = bytes_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "kernel": "pcg_cluster_kernel", "peak_kind": peak_kind,
-                "pcg_share_of_step": pcg_ms / tot_ms if tot_ms > 0 else None,
-                "avg_launch_us": avg_launch_s * 1e6, "iters_per_launch": iters_per_launch,
-                "us_per_iter": avg_launch_s * 1e6 / max(iters_per_launch, 1e-9),
-                "phase_ms_per_step": {k: v / args.steps for k, v in stats["phase_ms"].items() if v}}
-
-    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
-           "time_to_relres_s": ttr, "relres_reached_steps": len(reached),
-           "final_relres": infos[-1]["relres"], "final_rank": infos[-1]["rank"], "stop": infos[-1]["stop_name"],
-           "pcg_iters_per_step": stats["pcg_iters"] / args.steps,
-           "galerkin_cg_iters_per_step": sum(i["cg_iters"] for i in infos) / args.steps,
-           "roofline": roofline, "gpu_launches": stats["launches"], "clocks": clk.summary()}
-    g.close()
+    roofline = {"bound": "hbm", "achieved": head["pcg"]["achieved"], "peak": hbm, "unit": "GB/s",
+                "frac": head["pcg"]["achieved"] / hbm, "traffic": None, "kernel": "pcg_reg_kernel (cluster PCG)",
+                "peak_kind": peak_kind, "pcg_share_of_step": head["pcg"]["share_of_step"],
+                "avg_launch_us": head["pcg"]["avg_launch_us"], "iters_per_launch": head["pcg"]["iters_per_launch"],
+                "us_per_iter": head["pcg"]["us_per_iter"]}
+    out = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+           "config": cfg, "time_to_relres_s": head["time_to_relres_s"], "final_relres": head["final_relres"],
+           "final_rank": head["final_rank"], "stop": head["stop"],
+           "speedup_vs_fp64": head["value"] / forms["fp64"]["value"],
+           "roofline": roofline, "gpu_launches": head["gpu_launches"], "clocks": head["clocks"],
+           "forms": {k: {kk: vv for kk, vv in v.items() if kk not in ("clocks",)} for k, v in forms.items()}}
+    prec_e2e = CR_MIXED if args.precision == "mixed" else CR_FP64
 
     # end to end through the public API with host buffers (create + solve + factors + destroy)
     if not args.no_e2e:
@@ -278,7 +291,7 @@ def run_ours(args, rank, world, local_rank):
         for k in range(args.steps + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            with ConReg.from_problem(p, r_cap=args.r_max) as ge:
+            with ConReg.from_problem(p, r_cap=args.r_max, precision=prec_e2e) as ge:
                 info = ge.cr_solve(args.r_max, args.tau, args.relres)
                 U, Z, V = ge.cr_get_factors()
                 st = ge.cr_get_stats()

@@ -38,6 +38,8 @@ using namespace cr;
 namespace {
 thread_local std::string g_create_err;
 
+constexpr double kMixedPcgTol = 1e-6;
+
 enum {
   DS_UN2 = 0, DS_VN2 = 1, DS_NB = 2, DS_NA = 3, DS_DW = 4, /*5*/ DS_ZKZ = 6, DS_ZF = 7, DS_RN = 8, DS_V0 = 9,
   DS_GS = 16, DS_COUNT = 32
@@ -84,6 +86,10 @@ struct cr_problem {
   unsigned* gbar = nullptr;
   int* gerr = nullptr;
   int gal_nb = 0;
+  // float32 copies for the mixed form's inner Galerkin CG
+  float *fA1 = nullptr, *fA2 = nullptr, *fB1 = nullptr, *fB2 = nullptr, *fDg = nullptr, *fH = nullptr,
+        *fG = nullptr, *fF = nullptr, *fZ = nullptr, *fR = nullptr, *fPa = nullptr, *fPb = nullptr, *fQ = nullptr,
+        *fT2 = nullptr, *fT1 = nullptr, *fTH = nullptr, *fGw = nullptr, *fzb = nullptr;
   double *QL = nullptr, *CL = nullptr, *QR = nullptr, *CRm = nullptr, *Cx = nullptr, *Cx2 = nullptr, *Ep = nullptr,
          *CE = nullptr, *CP = nullptr, *Mc = nullptr, *T1 = nullptr, *T2 = nullptr, *gram = nullptr, *tmat = nullptr;
   int nQL = 0, nQR = 0, nQX = 0;
@@ -478,7 +484,10 @@ cr_status launch_pcg(cr_problem* p, int side, const double* b, double* x) {
   a.w = p->pw;
   a.dinv = p->pdinv;
   a.omt = p->pomt;
-  a.tol = p->opt.pcg_tol;
+  // The mixed form runs the sub-solves in float32 (inner products in float64);
+  // float32 vectors cannot resolve relative residuals much below 1e-6.
+  a.fp32 = p->opt.precision == CR_MIXED;
+  a.tol = a.fp32 ? std::max(p->opt.pcg_tol, kMixedPcgTol) : p->opt.pcg_tol;
   a.maxit = p->opt.pcg_maxit;
   a.stat = p->stat + side;
   a.force_generic = p->opt.pcg_kernel == 1;
@@ -608,6 +617,12 @@ cr_status grow_projections(cr_problem* p, int q) {
 // K (the paper's CG is unpreconditioned; the iterate it converges to is the
 // same Galerkin solution).  Device scalars: gs[k & 1] = <R_k, D^-1 R_k>,
 // gs[2] = <P, K P>, gs[3] = |F|^2, gs[4] = |R|^2.
+// float32 G_a = U^T diag(Omega_a) U for the inner solves of the mixed form.
+void mixed_G(cr_problem* p) {
+  const int64_t ld = p->rcap;
+  to_f32(ld * ld * p->m, p->G, p->fG, p->st);
+}
+
 cr_status do_project(cr_problem* p, double tol, cr_proj_info* info) {
   cudaStream_t st = p->st;
   const int j = p->j;
@@ -623,7 +638,56 @@ cr_status do_project(cr_problem* p, double tol, cr_proj_info* info) {
   int k = 0;
   double fn2 = 0.0, rr = 0.0;
   cr_status rc = CR_OK;
-  if (p->opt.galerkin_kernel == 0 && p->gal_nb > 0) {
+  if (p->opt.precision == CR_MIXED && p->gal_nb > 0) {
+    // Mixed form: float64 iterative refinement.  Each outer step forms the
+    // float64 residual R = F - K(Z) and solves K dZ = R to 1e-4 relative with
+    // the persistent CG in float32 (float32 copies of the projected matrices),
+    // then Z += dZ; the stopping test is on the float64 residual.
+    mat_dot(j, j, p->F, ld, p->F, ld, gs + 3, st);
+    TRY(readback(p, DS_GS + 3, 1, false));
+    fn2 = p->hs->ds[DS_GS + 3];
+    const int64_t r2 = ld * ld;
+    to_f32(r2, p->A1, p->fA1, st);
+    to_f32(r2, p->A2, p->fA2, st);
+    to_f32(r2, p->B1, p->fB1, st);
+    to_f32(r2, p->B2, p->fB2, st);
+    to_f32(r2, p->gDg, p->fDg, st);
+    to_f32(ld * p->m, p->H, p->fH, st);
+    mixed_G(p);
+    for (int outer = 0; outer < 40 && fn2 > 0.0; ++outer) {
+      galerkin_apply(p, p->Z, p->gQ);
+      mat_axpby(j, j, 1.0, p->F, ld, -1.0, p->gQ, ld, p->gR, ld, st);
+      mat_dot(j, j, p->gR, ld, p->gR, ld, gs + 4, st);
+      TRY(readback(p, DS_GS + 4, 1, false));
+      rr = p->hs->ds[DS_GS + 4];
+      if (!(rr > tol * tol * fn2)) break;
+      if (!std::isfinite(rr)) {
+        rc = fail(p, CR_ENOTCONV, "mixed Galerkin refinement produced a non-finite residual");
+        break;
+      }
+      to_f32(r2, p->gR, p->fF, st);
+      CUCHK(p, cudaMemsetAsync(p->fZ, 0, sizeof(float) * r2, st));
+      CUCHK(p, cudaMemsetAsync(p->gbar, 0, 2 * sizeof(unsigned), st));
+      CUCHK(p, cudaMemsetAsync(p->gerr, 0, sizeof(int), st));
+      cudaError_t ce = galerkin_cluster_f32_launch(j, p->m, ld, p->lam, p->fA1, p->fA2, p->fB1, p->fB2, p->fG,
+                                                   p->fH, p->fF, p->fDg, p->fZ, 1e-8 * rr, maxit, p->gout, st);
+      if (ce == cudaErrorNotSupported) {
+        cudaGetLastError();
+        ce = galerkin_cg_launch<float>(p->gal_nb, j, p->m, ld, p->lam, p->fA1, p->fA2, p->fB1, p->fB2, p->fG, p->fH,
+                                       p->fF, p->fDg, p->fZ, p->fR, p->fPa, p->fPb, p->fQ, p->fT2, p->fT1, p->fTH,
+                                       p->fGw, p->fzb, p->gpart, p->gbar, p->gerr, 1e-8 * rr, maxit, p->gout, st);
+      }
+      CUCHK(p, ce);
+      double out[3] = {0, 0, 0};
+      CUCHK(p, cudaMemcpyAsync(out, p->gout, sizeof(out), cudaMemcpyDeviceToHost, st));
+      p->d2h_bytes += (int64_t)sizeof(out);
+      TRY(sync(p));
+      k += (int)out[0];
+      if (out[2] == 3.0) return fail(p, CR_ETIMEOUT, "Galerkin CG grid barrier timed out");
+      add_f32(j, j, p->fZ, ld, p->Z, ld, st);
+      if (outer == 39) rc = fail(p, CR_ENOTCONV, "mixed Galerkin refinement did not converge");
+    }
+  } else if (p->opt.galerkin_kernel == 0 && p->gal_nb > 0) {
     // one cooperative launch runs the whole CG
     mat_dot(j, j, p->F, ld, p->F, ld, gs + 3, st);
     TRY(readback(p, DS_GS + 3, 1, false));
@@ -1072,7 +1136,11 @@ cr_status cr_create(const cr_problem_desc* d, const cr_options* o, cr_problem** 
     CK(upload(p, &d_lp, lp));
     CK(upload(p, &d_lr, lr));
     CK(upload(p, &d_lv, lv));
-    p->xl = DevXLocal{d_lp, d_lr, d_lv, d_rp, d_rc, d_rv};
+    std::vector<float> lvf(lv.begin(), lv.end()), rvf(rv.begin(), rv.end());
+    float *d_lvf, *d_rvf;
+    CK(upload(p, &d_lvf, lvf));
+    CK(upload(p, &d_rvf, rvf));
+    p->xl = DevXLocal{d_lp, d_lr, d_lv, d_rp, d_rc, d_rv, d_lvf, d_rvf};
   }
   // Omega o Y, Omega; norms |D|_F (via the m x m Gram products, all terms of
   // one sign pattern: |D|^2 = tr((OmY^T OmY)(X^T X))) and |Omega o Y|^2
@@ -1126,6 +1194,13 @@ cr_status cr_create(const cr_problem_desc* d, const cr_options* o, cr_problem** 
   CK(dalloc(p, &p->gout, 4));
   CK(dalloc(p, &p->gbar, 2));
   CK(dalloc(p, &p->gerr, 1));
+  if (opt.precision == CR_MIXED) {
+    for (float** b : {&p->fA1, &p->fA2, &p->fB1, &p->fB2, &p->fDg, &p->fF, &p->fZ, &p->fR, &p->fPa, &p->fPb, &p->fQ,
+                      &p->fT2, &p->fT1, &p->fzb})
+      CK(dalloc(p, b, r2));
+    for (float** b : {&p->fH, &p->fTH, &p->fGw}) CK(dalloc(p, b, (size_t)rc * m));
+    CK(dalloc(p, &p->fG, r2 * m));
+  }
   CK(dalloc(p, &p->stat, 2));
   CK(dalloc(p, &p->ds, DS_COUNT));
   // residual-norm bases and core workspaces

@@ -54,6 +54,8 @@ struct DevXLocal {
   const int* xr_ptr = nullptr;   // [nx + 1]
   const int* xr_col = nullptr;
   const double* xr_val = nullptr;
+  const float* lx_valf = nullptr;  // float32 copies (mixed form)
+  const float* xr_valf = nullptr;
 };
 
 // Scalars the host reads back after a PCG solve.
@@ -90,6 +92,7 @@ struct PcgArgs {
   int maxit;
   PcgStat* stat;           // device
   int force_generic;       // 1: always use the shared/global-memory kernel
+  int fp32;                // 1: float32 vectors and arithmetic, float64 inner products and scalars
 };
 
 // ---------------------------------------------------------------- cr_pcg.cu
@@ -143,11 +146,20 @@ void batched_gemv(int j, int m, const double* G, int64_t ldg, int64_t gstride, c
 // ---------------------------------------------------------------- cr_galerkin.cu
 // CTAs of the persistent Galerkin CG (one per SM), 0 if the kernel cannot run.
 int galerkin_grid_size();
-cudaError_t galerkin_cg_launch(int nb, int j, int m, int64_t ld, double lam, const double* A1, const double* A2,
-                               const double* B1, const double* B2, const double* G, const double* H,
-                               const double* F, const double* Dg, double* Z, double* R, double* Pa, double* Pb,
-                               double* Q, double* T2, double* T1, double* TH, double* Gw, double* zb, double* part,
-                               unsigned* bar, int* err, double tol2, int maxit, double* out, cudaStream_t st);
+// T = double (float64 form) or float (inner solve of the mixed form)
+template <class T>
+cudaError_t galerkin_cg_launch(int nb, int j, int m, int64_t ld, double lam, const T* A1, const T* A2, const T* B1,
+                               const T* B2, const T* G, const T* H, const T* F, const T* Dg, T* Z, T* R, T* Pa,
+                               T* Pb, T* Q, T* T2, T* T1, T* TH, T* Gw, T* zb, double* part, unsigned* bar,
+                               int* err, double tol2, int maxit, double* out, cudaStream_t st);
+
+// Single-cluster float32 Galerkin CG (inner solves of the mixed form, j <= 128,
+// m <= 128); cudaErrorNotSupported when the sizes do not fit.  Solves
+// K32 Z = F from Z = 0 until |F - K32 Z|^2 <= tol2.  out: iterations, |R|^2, status.
+cudaError_t galerkin_cluster_f32_launch(int j, int m, int64_t ld, double lam, const float* A1, const float* A2,
+                                        const float* B1, const float* B2, const float* G, const float* H,
+                                        const float* F, const float* Dg, float* Z, double tol2, int maxit,
+                                        double* out, cudaStream_t st);
 
 }  // namespace cr
 
@@ -183,6 +195,10 @@ void build_core(int m, int j, const double* Z, int64_t ldz, double lam, double* 
 // Dg(p, q) = diagonal of the projected operator at Z(p, q) (Jacobi preconditioner of the Galerkin CG)
 void galerkin_diag(int j, int m, const double* A1, const double* A2, const double* B1, const double* B2,
                    const double* G, const double* H, int64_t ld, double lam, double* Dg, cudaStream_t st);
+// y[i] = (float) x[i]
+void to_f32(int64_t n, const double* x, float* y, cudaStream_t st);
+// y(i, l) += (double) x(i, l)
+void add_f32(int r, int c, const float* x, int64_t ldx, double* y, int64_t ldy, cudaStream_t st);
 // Zp = R ./ Dg, out0 = <R, Zp>, out1 = <R, R>
 void precond_dots(int j, const double* R, const double* Dg, int64_t ld, double* Zp, double* out0, double* out1,
                   cudaStream_t st);

@@ -18,6 +18,8 @@
 // launch is read with ld.global.cg (L2), never from a possibly stale L1 line.
 // The grid barrier spins with a bound; on timeout it raises an error word that
 // makes every CTA leave, and the host reports CR_ETIMEOUT.
+#include <algorithm>
+
 #include "cr_common.cuh"
 
 namespace cr {
@@ -27,12 +29,13 @@ namespace {
 constexpr int kGThreads = 256;
 constexpr int TS = 8;
 
+template <class T>
 struct GalArgs {
   int j, m, nb;
   int64_t ld;
   double lam;
-  const double *A1, *A2, *B1, *B2, *G, *H, *F, *Dg;
-  double *Z, *R, *Pa, *Pb, *Q, *T2, *T1, *TH, *Gw, *zb;
+  const T *A1, *A2, *B1, *B2, *G, *H, *F, *Dg;
+  T *Z, *R, *Pa, *Pb, *Q, *T2, *T1, *TH, *Gw, *zb;
   double* part;        // [nb * 4]
   unsigned* bar;       // [0] arrivals, [1] generation
   int* err;            // timeout flag
@@ -42,9 +45,11 @@ struct GalArgs {
 };
 
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ float ldcg(const float* p) { return __ldcg(p); }
 
 // Grid-wide barrier with a bounded spin.  Returns false if the error word is set.
-__device__ __forceinline__ bool grid_barrier(const GalArgs& a) {
+template <class T>
+__device__ __forceinline__ bool grid_barrier(const GalArgs<T>& a) {
   __syncthreads();
   __shared__ int ok;
   if (threadIdx.x == 0) {
@@ -86,8 +91,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // Sum NV values over the CTA (fixed order) and store them at part[blockIdx * 4 + q].
-template <int NV>
-__device__ void cta_partial(double (&v)[NV], const GalArgs& a) {
+template <int NV, class T>
+__device__ void cta_partial(double (&v)[NV], const GalArgs<T>& a) {
   __shared__ double scr[32 * 4];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -107,8 +112,8 @@ __device__ void cta_partial(double (&v)[NV], const GalArgs& a) {
 }
 
 // After a barrier: totals of the per-CTA partials, same order in every CTA.
-template <int NV>
-__device__ void grid_total(const GalArgs& a, double (&out)[NV]) {
+template <int NV, class T>
+__device__ void grid_total(const GalArgs<T>& a, double (&out)[NV]) {
   __shared__ double tot[4];
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
@@ -128,10 +133,10 @@ __device__ void grid_total(const GalArgs& a, double (&out)[NV]) {
 
 // One 8x8 output tile of sum_k A(i, k) B(k, l); 256 threads = 64 outputs x 4
 // k-groups.  Returns this thread's partial; combine with tile_reduce.
-template <class GA, class GB>
-__device__ __forceinline__ double tile_term(int i0, int l0, int M, int N, int K, GA ga, GB gb, double acc) {
-  __shared__ double As[32][TS + 1];
-  __shared__ double Bs[32][TS + 1];
+template <class T, class GA, class GB>
+__device__ __forceinline__ T tile_term(int i0, int l0, int M, int N, int K, GA ga, GB gb, T acc) {
+  __shared__ T As[32][TS + 1];
+  __shared__ T Bs[32][TS + 1];
   const int tid = threadIdx.x;
   const int o = tid & 63, g = tid >> 6;
   const int oi = o & 7, ol = o >> 3;
@@ -139,12 +144,12 @@ __device__ __forceinline__ double tile_term(int i0, int l0, int M, int N, int K,
     {
       const int ii = tid & 7, kk = tid >> 3;
       const int i = i0 + ii, k = k0 + kk;
-      As[kk][ii] = (i < M && k < K) ? ga(i, k) : 0.0;
+      As[kk][ii] = (i < M && k < K) ? ga(i, k) : (T)0;
     }
     {
       const int kk = tid & 31, ll = tid >> 5;
       const int l = l0 + ll, k = k0 + kk;
-      Bs[kk][ll] = (l < N && k < K) ? gb(k, l) : 0.0;
+      Bs[kk][ll] = (l < N && k < K) ? gb(k, l) : (T)0;
     }
     __syncthreads();
 #pragma unroll
@@ -156,12 +161,13 @@ __device__ __forceinline__ double tile_term(int i0, int l0, int M, int N, int K,
 
 // Add the 4 k-group partials in order; threads 0..63 return the output of
 // (i0 + (t & 7), l0 + (t >> 3)), others return 0 with valid = false.
-__device__ __forceinline__ double tile_reduce(double acc, bool& valid) {
-  __shared__ double red[4][64];
+template <class T>
+__device__ __forceinline__ T tile_reduce(T acc, bool& valid) {
+  __shared__ T red[4][64];
   const int tid = threadIdx.x;
   red[tid >> 6][tid & 63] = acc;
   __syncthreads();
-  double v = 0.0;
+  T v = (T)0;
   valid = tid < 64;
   if (valid) v = ((red[0][tid] + red[1][tid]) + red[2][tid]) + red[3][tid];
   __syncthreads();
@@ -169,7 +175,8 @@ __device__ __forceinline__ double tile_reduce(double acc, bool& valid) {
 }
 
 // K(X) -> Q for X = Xin (phases A, B, C); returns <X, Q> partial of this CTA in pq.
-__device__ bool apply_K(const GalArgs& a, const double* X, double& pq) {
+template <class T>
+__device__ bool apply_K(const GalArgs<T>& a, const T* X, double& pq) {
   const int j = a.j, m = a.m;
   const int64_t ld = a.ld;
   const int nt = (j + TS - 1) / TS, ntm = (m + TS - 1) / TS;
@@ -185,12 +192,12 @@ __device__ bool apply_K(const GalArgs& a, const double* X, double& pq) {
       which = 2; ti = (it - 2 * nt * nt) % nt; tl = (it - 2 * nt * nt) / nt;
     }
     const int N = which == 2 ? m : j;
-    const double* Bm = which == 0 ? a.B2 : which == 1 ? a.B1 : a.H;
-    double* out = which == 0 ? a.T2 : which == 1 ? a.T1 : a.TH;
-    double acc = tile_term(ti * TS, tl * TS, j, N, j, [&](int i, int k) { return ldcg(X + i + k * ld); },
-                           [&](int k, int l) { return Bm[k + l * ld]; }, 0.0);
+    const T* Bm = which == 0 ? a.B2 : which == 1 ? a.B1 : a.H;
+    T* out = which == 0 ? a.T2 : which == 1 ? a.T1 : a.TH;
+    T acc = tile_term<T>(ti * TS, tl * TS, j, N, j, [&](int i, int k) { return ldcg(X + i + k * ld); },
+                         [&](int k, int l) { return Bm[k + l * ld]; }, (T)0);
     bool v;
-    const double r = tile_reduce(acc, v);
+    const T r = tile_reduce<T>(acc, v);
     if (v) {
       const int i = ti * TS + (threadIdx.x & 7), l = tl * TS + (threadIdx.x >> 3);
       if (i < j && l < N) out[i + l * ld] = r;
@@ -202,13 +209,13 @@ __device__ bool apply_K(const GalArgs& a, const double* X, double& pq) {
   for (int it = blockIdx.x; it < m * nr; it += a.nb) {
     const int al = it / nr, rt = it % nr;
     const int i = rt * 64 + (threadIdx.x & 63), g = threadIdx.x >> 6;
-    const double* Ga = a.G + (int64_t)al * ld * ld;
-    double acc = 0.0;
+    const T* Ga = a.G + (int64_t)al * ld * ld;
+    T acc = (T)0;
     if (i < j) {
       const int q0 = g * ((j + 3) / 4), q1 = min(j, q0 + (j + 3) / 4);
       for (int q = q0; q < q1; ++q) acc = fma(Ga[i + q * ld], ldcg(a.TH + q + al * ld), acc);
     }
-    __shared__ double rb[4][64];
+    __shared__ T rb[4][64];
     rb[g][threadIdx.x & 63] = acc;
     __syncthreads();
     if (threadIdx.x < 64 && i < j)
@@ -218,26 +225,27 @@ __device__ bool apply_K(const GalArgs& a, const double* X, double& pq) {
   if (!grid_barrier(a)) return false;
   // C
   double dotpq = 0.0;
-  const double lam = a.lam;
+  const T lam = (T)a.lam;
+  const T lam2 = (T)(2.0 * a.lam);
   for (int it = blockIdx.x; it < nt * nt; it += a.nb) {
     const int ti = it % nt, tl = it / nt;
     const int i0 = ti * TS, l0 = tl * TS;
-    double acc = 0.0;
-    acc = tile_term(i0, l0, j, j, j, [&](int i, int k) { return 2.0 * lam * a.A1[i + k * ld]; },
-                    [&](int k, int l) { return ldcg(a.T1 + k + l * ld); }, acc);
-    acc = tile_term(i0, l0, j, j, j, [&](int i, int k) { return lam * a.A2[i + k * ld]; },
-                    [&](int k, int l) { return ldcg(X + k + l * ld); }, acc);
-    acc = tile_term(i0, l0, j, j, m, [&](int i, int k) { return ldcg(a.Gw + i + k * ld); },
-                    [&](int k, int l) { return a.H[l + k * ld]; }, acc);
+    T acc = (T)0;
+    acc = tile_term<T>(i0, l0, j, j, j, [&](int i, int k) { return lam2 * a.A1[i + k * ld]; },
+                       [&](int k, int l) { return ldcg(a.T1 + k + l * ld); }, acc);
+    acc = tile_term<T>(i0, l0, j, j, j, [&](int i, int k) { return lam * a.A2[i + k * ld]; },
+                       [&](int k, int l) { return ldcg(X + k + l * ld); }, acc);
+    acc = tile_term<T>(i0, l0, j, j, m, [&](int i, int k) { return ldcg(a.Gw + i + k * ld); },
+                       [&](int k, int l) { return a.H[l + k * ld]; }, acc);
     bool v;
-    const double r = tile_reduce(acc, v);
+    const T r = tile_reduce<T>(acc, v);
     if (v) {
       const int i = i0 + (threadIdx.x & 7), l = l0 + (threadIdx.x >> 3);
       if (i < j && l < j) {
         const int64_t o = i + l * ld;
-        const double q = fma(lam, ldcg(a.T2 + o), r);
+        const T q = fma(lam, ldcg(a.T2 + o), r);
         a.Q[o] = q;
-        dotpq = fma(ldcg(X + o), q, dotpq);
+        dotpq += (double)ldcg(X + o) * (double)q;
       }
     }
   }
@@ -245,7 +253,8 @@ __device__ bool apply_K(const GalArgs& a, const double* X, double& pq) {
   return true;
 }
 
-__global__ void __launch_bounds__(kGThreads, 1) galerkin_cg_kernel(const GalArgs a) {
+template <class T>
+__global__ void __launch_bounds__(kGThreads, 1) galerkin_cg_kernel(const GalArgs<T> a) {
   const int j = a.j;
   const int64_t ld = a.ld;
   const int64_t tot = (int64_t)j * j;
@@ -261,12 +270,12 @@ __global__ void __launch_bounds__(kGThreads, 1) galerkin_cg_kernel(const GalArgs
     double v[2] = {0.0, 0.0};
     for (int64_t t = e0 + threadIdx.x; t < e1; t += blockDim.x) {
       const int64_t o = (t % j) + (t / j) * ld;
-      const double r = a.F[o] - ldcg(a.Q + o);
-      const double z = r / a.Dg[o];
+      const T r = a.F[o] - ldcg(a.Q + o);
+      const T z = r / a.Dg[o];
       a.R[o] = r;
       a.Pa[o] = z;
-      v[0] = fma(r, z, v[0]);
-      v[1] = fma(r, r, v[1]);
+      v[0] += (double)r * (double)z;
+      v[1] += (double)r * (double)r;
     }
     cta_partial<2>(v, a);
   }
@@ -278,8 +287,8 @@ __global__ void __launch_bounds__(kGThreads, 1) galerkin_cg_kernel(const GalArgs
     rr = t2[1];
   }
   {
-    double* X = a.Pa;
-    double* Xn = a.Pb;
+    T* X = a.Pa;
+    T* Xn = a.Pb;
     while (rr > a.tol2) {
       if (k >= a.maxit) {
         status = 1;
@@ -297,25 +306,25 @@ __global__ void __launch_bounds__(kGThreads, 1) galerkin_cg_kernel(const GalArgs
         status = 2;
         break;
       }
-      const double alpha = rho / pqt[0];
+      const T alpha = (T)(rho / pqt[0]);
       {
         double v[2] = {0.0, 0.0};
         for (int64_t t = e0 + threadIdx.x; t < e1; t += blockDim.x) {
           const int64_t o = (t % j) + (t / j) * ld;
           a.Z[o] = fma(alpha, ldcg(X + o), a.Z[o]);
-          const double r = fma(-alpha, ldcg(a.Q + o), a.R[o]);
+          const T r = fma(-alpha, ldcg(a.Q + o), a.R[o]);
           a.R[o] = r;
-          const double z = r / a.Dg[o];
+          const T z = r / a.Dg[o];
           a.zb[o] = z;
-          v[0] = fma(r, z, v[0]);
-          v[1] = fma(r, r, v[1]);
+          v[0] += (double)r * (double)z;
+          v[1] += (double)r * (double)r;
         }
         cta_partial<2>(v, a);
       }
       if (!grid_barrier(a)) goto timeout;
       double t2[2];
       grid_total<2>(a, t2);
-      const double beta = rho > 0.0 ? t2[0] / rho : 0.0;
+      const T beta = (T)(rho > 0.0 ? t2[0] / rho : 0.0);
       rho = t2[0];
       rr = t2[1];
       ++k;
@@ -324,7 +333,7 @@ __global__ void __launch_bounds__(kGThreads, 1) galerkin_cg_kernel(const GalArgs
         Xn[o] = fma(beta, ldcg(X + o), a.zb[o]);
       }
       if (!grid_barrier(a)) goto timeout;
-      double* tmp = X;
+      T* tmp = X;
       X = Xn;
       Xn = tmp;
     }
@@ -349,19 +358,20 @@ int galerkin_grid_size() {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, galerkin_cg_kernel, kGThreads, 0) != cudaSuccess || per < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, galerkin_cg_kernel<double>, kGThreads, 0) != cudaSuccess ||
+      per < 1) {
     cudaGetLastError();
     return 0;
   }
   return sms;
 }
 
-cudaError_t galerkin_cg_launch(int nb, int j, int m, int64_t ld, double lam, const double* A1, const double* A2,
-                               const double* B1, const double* B2, const double* G, const double* H,
-                               const double* F, const double* Dg, double* Z, double* R, double* Pa, double* Pb,
-                               double* Q, double* T2, double* T1, double* TH, double* Gw, double* zb, double* part,
-                               unsigned* bar, int* err, double tol2, int maxit, double* out, cudaStream_t st) {
-  GalArgs a{};
+template <class T>
+cudaError_t galerkin_cg_launch(int nb, int j, int m, int64_t ld, double lam, const T* A1, const T* A2, const T* B1,
+                               const T* B2, const T* G, const T* H, const T* F, const T* Dg, T* Z, T* R, T* Pa,
+                               T* Pb, T* Q, T* T2, T* T1, T* TH, T* Gw, T* zb, double* part, unsigned* bar,
+                               int* err, double tol2, int maxit, double* out, cudaStream_t st) {
+  GalArgs<T> a{};
   a.j = j;
   a.m = m;
   a.nb = nb;
@@ -393,7 +403,348 @@ cudaError_t galerkin_cg_launch(int nb, int j, int m, int64_t ld, double lam, con
   a.out = out;
   void* args[] = {&a};
   count_launch();
-  return cudaLaunchCooperativeKernel((const void*)galerkin_cg_kernel, dim3(nb), dim3(kGThreads), args, 0, st);
+  return cudaLaunchCooperativeKernel((const void*)galerkin_cg_kernel<T>, dim3(nb), dim3(kGThreads), args, 0, st);
+}
+
+template cudaError_t galerkin_cg_launch<double>(int, int, int, int64_t, double, const double*, const double*,
+                                                const double*, const double*, const double*, const double*,
+                                                const double*, const double*, double*, double*, double*, double*,
+                                                double*, double*, double*, double*, double*, double*, double*,
+                                                unsigned*, int*, double, int, double*, cudaStream_t);
+template cudaError_t galerkin_cg_launch<float>(int, int, int, int64_t, double, const float*, const float*,
+                                               const float*, const float*, const float*, const float*, const float*,
+                                               const float*, float*, float*, float*, float*, float*, float*, float*,
+                                               float*, float*, float*, double*, unsigned*, int*, double, int, double*,
+                                               cudaStream_t);
+
+}  // namespace cr
+
+// ---------------------------------------------------------------------------
+// Single-cluster float32 Galerkin CG for the inner solves of the mixed form
+// (j <= 128, m <= 128).  The columns of the CG matrices are split over the
+// CTAs of one cluster; every CTA keeps a full copy of the current search
+// direction X and of Gw = [G_a X h_a]_a in shared memory, refreshed by an
+// all-gather over distributed shared memory, so every product is local:
+//   T2 = X B2(:, own), T1 = X B1(:, own), TH = X H(:, own a), Gw(:, own a) = G_a TH(:, a)
+//   Q(:, own) = lam T2 + 2 lam A1 T1 + lam A2 X(:, own) + Gw H(own, :)^T
+// Inner products and CG scalars are double-float (cr_df.cuh), reduced in a
+// fixed order (threads, warps, CTAs in rank order).  Four cluster barriers
+// per iteration, no grid barrier, no launch.
+#include <cooperative_groups.h>
+
+#include "cr_df.cuh"
+
+namespace cr {
+namespace {
+
+namespace cgc = cooperative_groups;
+
+constexpr int kClThreads = 512;
+constexpr int kClMax = 16;
+
+struct GalClArgs {
+  int j, m, cw, aw;  // rank, injections, columns per CTA, injections per CTA
+  int64_t ld;
+  float lam;
+  const float *A1, *A2, *B1, *B2, *G, *H, *F, *Dg;
+  float* Z;
+  float tol2;  // stop when |R|^2 <= tol2
+  int maxit;
+  double* out;
+};
+
+__device__ __forceinline__ DF cl_block_df(DF v, DF* scr) {
+  // returns the CTA sum (valid in thread 0)
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum_df(v);
+  if (lane == 0) scr[wid] = v;
+  __syncthreads();
+  DF t{0.f, 0.f};
+  if (wid == 0) {
+    t = lane < nw ? scr[lane] : DF{0.f, 0.f};
+    t = warp_sum_df(t);
+  }
+  __syncthreads();
+  return t;
+}
+
+// Copy into buf every element whose block (of `bw` consecutive elements) is
+// owned by another CTA, from that CTA's buf.  Eight independent loads are
+// issued per thread before their stores, so the distributed-shared-memory
+// latencies overlap instead of adding up.
+__device__ __forceinline__ void gather_blocks(cgc::cluster_group& cl, float* buf, int total, int bw, int rank) {
+  const int nth = blockDim.x;
+  for (int t0 = threadIdx.x; t0 < total; t0 += 8 * nth) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = t0 + u * nth;
+      const int owner = idx < total ? idx / bw : rank;
+      v[u] = owner != rank ? cl.map_shared_rank(buf, (unsigned)owner)[idx] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = t0 + u * nth;
+      if (idx < total && idx / bw != rank) buf[idx] = v[u];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kClThreads, 1) galerkin_cluster_f32_kernel(const GalClArgs a) {
+  cgc::cluster_group cl = cgc::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const int j = a.j, m = a.m, cw = a.cw, aw = a.aw;
+  const int64_t ld = a.ld;
+  const int c0 = min(j, rank * cw), c1 = min(j, c0 + cw), nc = c1 - c0;
+  const int a0 = min(m, rank * aw), a1 = min(m, a0 + aw), na = a1 - a0;
+  extern __shared__ __align__(16) float fsm[];
+  float* Xf = fsm;                 // j x j (ld j): full search direction
+  float* Gwf = Xf + j * j;         // j x m (ld j)
+  float* Zo = Gwf + j * m;         // own blocks, j x cw each (ld j)
+  float* Ro = Zo + j * cw;
+  float* zo = Ro + j * cw;
+  float* Qo = zo + j * cw;
+  float* T1o = Qo + j * cw;
+  float* T2o = T1o + j * cw;
+  float* THo = T2o + j * cw;       // j x aw
+  DF* scr = reinterpret_cast<DF*>(THo + j * aw);  // [32]
+  DF* red = scr + 32;              // [2][4]
+  float* scal = reinterpret_cast<float*>(red + 8);  // [8]
+  float* Xo = Xf + (int64_t)c0 * j;  // own columns of X inside the full copy
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const float lam = a.lam, lam2 = 2.f * a.lam;
+
+  // init: Z = 0, R = F, z = R / D, P = z
+  DF rz{0.f, 0.f}, rr{0.f, 0.f};
+  for (int t = tid; t < j * nc; t += nth) {
+    const int i = t % j, lc = t / j;
+    const int64_t o = i + (int64_t)(c0 + lc) * ld;
+    const float r = a.F[o], z = r / a.Dg[o];
+    Zo[t] = 0.f;
+    Ro[t] = r;
+    zo[t] = z;
+    Xo[t] = z;
+    rz = df_add(rz, df_prod(r, z));
+    rr = df_add(rr, df_prod(r, r));
+  }
+  {
+    const DF s0 = cl_block_df(rz, scr);
+    const DF s1 = cl_block_df(rr, scr);
+    if (tid == 0) {
+      red[0] = s0;
+      red[1] = s1;
+    }
+  }
+  cl.sync();
+  if (tid < 32) {
+    DF g{0.f, 0.f}, h{0.f, 0.f};
+    if (tid < C) {
+      const DF* rm = cl.map_shared_rank(red, tid);
+      g = rm[0];
+      h = rm[1];
+    }
+    g = warp_sum_df(g);
+    h = warp_sum_df(h);
+    if (tid == 0) {
+      reinterpret_cast<DF*>(scal)[0] = g;
+      reinterpret_cast<DF*>(scal)[1] = h;
+    }
+  }
+  __syncthreads();
+  DF rho = reinterpret_cast<DF*>(scal)[0];
+  DF rrt = reinterpret_cast<DF*>(scal)[1];
+  int it = 0, status = 0;
+  while (rrt.hi > a.tol2) {
+    if (it >= a.maxit) {
+      status = 1;
+      break;
+    }
+    cl.sync();  // B1: own columns of X published
+    // all-gather X: copy the other CTAs' column blocks
+    gather_blocks(cl, Xf, j * j, j * cw, rank);
+    __syncthreads();
+    // T2, T1 on own columns; TH on own injections
+    for (int t = tid; t < j * nc; t += nth) {
+      const int i = t % j, lc = t / j;
+      const float* b2 = a.B2 + (int64_t)(c0 + lc) * ld;
+      const float* b1 = a.B1 + (int64_t)(c0 + lc) * ld;
+      float s2 = 0.f, s1 = 0.f;
+      for (int k = 0; k < j; ++k) {
+        const float x = Xf[i + k * j];
+        s2 = fmaf(x, __ldg(b2 + k), s2);
+        s1 = fmaf(x, __ldg(b1 + k), s1);
+      }
+      T2o[t] = s2;
+      T1o[t] = s1;
+    }
+    for (int t = tid; t < j * na; t += nth) {
+      const int i = t % j, la = t / j;
+      const float* h = a.H + (int64_t)(a0 + la) * ld;
+      float s = 0.f;
+      for (int k = 0; k < j; ++k) s = fmaf(Xf[i + k * j], __ldg(h + k), s);
+      THo[t] = s;
+    }
+    __syncthreads();
+    for (int t = tid; t < j * na; t += nth) {
+      const int i = t % j, la = t / j;
+      const float* g = a.G + (int64_t)(a0 + la) * ld * ld;
+      float s = 0.f;
+      for (int q = 0; q < j; ++q) s = fmaf(__ldg(g + i + (int64_t)q * ld), THo[q + la * j], s);
+      Gwf[i + (a0 + la) * j] = s;
+    }
+    cl.sync();  // B2: own columns of Gw published
+    gather_blocks(cl, Gwf, j * m, j * aw, rank);
+    __syncthreads();
+    // Q on own columns and <X, Q>
+    DF pq{0.f, 0.f};
+    for (int t = tid; t < j * nc; t += nth) {
+      const int i = t % j, lc = t / j;
+      const int l = c0 + lc;
+      float s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      for (int k = 0; k < j; ++k) {
+        s1 = fmaf(__ldg(a.A1 + i + (int64_t)k * ld), T1o[k + lc * j], s1);
+        s2 = fmaf(__ldg(a.A2 + i + (int64_t)k * ld), Xo[k + lc * j], s2);
+      }
+      for (int al = 0; al < m; ++al) s3 = fmaf(Gwf[i + al * j], __ldg(a.H + l + (int64_t)al * ld), s3);
+      const float q = lam * T2o[t] + lam2 * s1 + lam * s2 + s3;
+      Qo[t] = q;
+      pq = df_add(pq, df_prod(Xo[t], q));
+    }
+    {
+      const DF s = cl_block_df(pq, scr);
+      if (tid == 0) red[2] = s;
+    }
+    cl.sync();  // B3
+    if (tid < 32) {
+      DF g{0.f, 0.f};
+      if (tid < C) g = cl.map_shared_rank(red, tid)[2];
+      g = warp_sum_df(g);
+      if (tid == 0) {
+        float ok = (g.hi > 0.f && isfinite(g.hi)) ? 1.f : 0.f;
+        const DF alpha = ok > 0.f ? df_div(rho, g) : DF{0.f, 0.f};
+        scal[4] = ok;
+        scal[5] = alpha.hi;
+      }
+    }
+    __syncthreads();
+    if (scal[4] == 0.f) {
+      status = 2;
+      break;
+    }
+    const float alpha = scal[5];
+    DF rz2{0.f, 0.f}, rr2{0.f, 0.f};
+    for (int t = tid; t < j * nc; t += nth) {
+      const int i = t % j, lc = t / j;
+      const int64_t o = i + (int64_t)(c0 + lc) * ld;
+      Zo[t] = fmaf(alpha, Xo[t], Zo[t]);
+      const float r = fmaf(-alpha, Qo[t], Ro[t]);
+      Ro[t] = r;
+      const float z = r / a.Dg[o];
+      zo[t] = z;
+      rz2 = df_add(rz2, df_prod(r, z));
+      rr2 = df_add(rr2, df_prod(r, r));
+    }
+    {
+      const DF s0 = cl_block_df(rz2, scr);
+      const DF s1 = cl_block_df(rr2, scr);
+      if (tid == 0) {
+        red[4] = s0;
+        red[5] = s1;
+      }
+    }
+    cl.sync();  // B4
+    if (tid < 32) {
+      DF g{0.f, 0.f}, h{0.f, 0.f};
+      if (tid < C) {
+        const DF* rm = cl.map_shared_rank(red, tid);
+        g = rm[4];
+        h = rm[5];
+      }
+      g = warp_sum_df(g);
+      h = warp_sum_df(h);
+      if (tid == 0) {
+        const DF beta = rho.hi > 0.f ? df_div(g, rho) : DF{0.f, 0.f};
+        reinterpret_cast<DF*>(scal)[0] = g;
+        reinterpret_cast<DF*>(scal)[1] = h;
+        scal[6] = beta.hi;
+      }
+    }
+    __syncthreads();
+    rho = reinterpret_cast<DF*>(scal)[0];
+    rrt = reinterpret_cast<DF*>(scal)[1];
+    const float beta = scal[6];
+    for (int t = tid; t < j * nc; t += nth) Xo[t] = fmaf(beta, Xo[t], zo[t]);
+    ++it;
+  }
+  for (int t = tid; t < j * nc; t += nth) {
+    const int i = t % j, lc = t / j;
+    a.Z[i + (int64_t)(c0 + lc) * ld] = Zo[t];
+  }
+  cl.sync();  // no CTA leaves while another may read its shared memory
+  if (rank == 0 && tid == 0) {
+    a.out[0] = (double)it;
+    a.out[1] = (double)rrt.hi + (double)rrt.lo;
+    a.out[2] = (double)status;
+  }
+}
+
+size_t gal_cl_smem(int j, int m, int cw, int aw) {
+  return sizeof(float) * ((size_t)j * j + (size_t)j * m + 7 * (size_t)j * cw + (size_t)j * aw) + sizeof(DF) * 40 +
+         sizeof(float) * 8 + 64;
+}
+
+}  // namespace
+
+// Launch the single-cluster float32 Galerkin CG if it fits (j <= 128, m <= 128);
+// returns cudaErrorNotSupported otherwise.
+cudaError_t galerkin_cluster_f32_launch(int j, int m, int64_t ld, double lam, const float* A1, const float* A2,
+                                        const float* B1, const float* B2, const float* G, const float* H,
+                                        const float* F, const float* Dg, float* Z, double tol2, int maxit,
+                                        double* out, cudaStream_t st) {
+  if (j < 1 || j > 128 || m > 128) return cudaErrorNotSupported;
+  const int C = std::min(kClMax, j);
+  const int cw = (j + C - 1) / C, aw = (m + C - 1) / C;
+  const size_t smem = gal_cl_smem(j, m, cw, aw);
+  if (smem > 227 * 1024) return cudaErrorNotSupported;
+  cudaError_t e = cudaFuncSetAttribute(galerkin_cluster_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       227 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(galerkin_cluster_f32_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  GalClArgs a{};
+  a.j = j;
+  a.m = m;
+  a.cw = cw;
+  a.aw = aw;
+  a.ld = ld;
+  a.lam = (float)lam;
+  a.A1 = A1;
+  a.A2 = A2;
+  a.B1 = B1;
+  a.B2 = B2;
+  a.G = G;
+  a.H = H;
+  a.F = F;
+  a.Dg = Dg;
+  a.Z = Z;
+  a.tol2 = (float)tol2;
+  a.maxit = maxit;
+  a.out = out;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(kClThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  count_launch();
+  return cudaLaunchKernelEx(&cfg, galerkin_cluster_f32_kernel, a);
 }
 
 }  // namespace cr

@@ -21,6 +21,7 @@
 #include <cooperative_groups.h>
 
 #include "cr_common.cuh"
+#include "cr_df.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -285,16 +286,45 @@ __device__ __forceinline__ uint32_t mapa_u32(uint32_t a, uint32_t rank) {
   return r;
 }
 
-__device__ __forceinline__ double ld_dsm(uint32_t a) {
+template <class T>
+__device__ __forceinline__ T ld_dsm(uint32_t a);
+
+template <>
+__device__ __forceinline__ double ld_dsm<double>(uint32_t a) {
   double v;
   asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
   return v;
 }
 
+template <>
+__device__ __forceinline__ float ld_dsm<float>(uint32_t a) {
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+  return v;
+}
+
+template <class T>
+__device__ __forceinline__ T ld_sh(uint32_t a);
+
+template <>
+__device__ __forceinline__ double ld_sh<double>(uint32_t a) {
+  double v;
+  asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
+  return v;
+}
+
+template <>
+__device__ __forceinline__ float ld_sh<float>(uint32_t a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+  return v;
+}
+
 constexpr int kRegSlots = 6;
 
-template <int KIND, int VPT>
+template <int KIND, int VPT, class T>
 __global__ void __launch_bounds__(kPcgThreads, 1) pcg_reg_kernel(const PcgArgs A) {
+  constexpr bool kF32 = sizeof(T) == sizeof(float);
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
@@ -304,44 +334,46 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_reg_kernel(const PcgArgs A
   const int nloc = max(0, min(L.n - beg, chunk));
   const int m = A.m;
   extern __shared__ __align__(16) double sm[];
-  // layout: [zero word pad 2] [ub0 chunk] [ub1 chunk] [tb chunk] [red 8] [ypart m] [sS m] [sY m] [scr 128] [scal 8]
-  double* zero = sm;
-  double* ub0 = sm + 2;
-  double* ub1 = ub0 + chunk;
-  double* tb = ub1 + chunk;
-  double* red = tb + chunk;
+  // layout (doubles): [red 8] [ypart m] [sS m] [sY m] [scr 128] [scal 8]; then (T): [zero 2] [ub0] [ub1] [tb]
+  double* red = sm;
   double* ypart = red + 8;
   double* sS = ypart + m;
   double* sY = sS + m;
   double* scr = sY + m;
   double* scal = scr + 128;
-  const uint32_t off_ub1 = (uint32_t)(chunk * sizeof(double));
-  const uint32_t off_tb = (uint32_t)(2 * chunk * sizeof(double));
-  const double lam = A.lam;
+  T* zero = reinterpret_cast<T*>(scal + 8);
+  T* ub0 = zero + 2;
+  T* ub1 = ub0 + chunk;
+  T* tb = ub1 + chunk;
+  const uint32_t off_ub1 = (uint32_t)(chunk * sizeof(T));
+  const uint32_t off_tb = (uint32_t)(2 * chunk * sizeof(T));
+  const T lam = (T)A.lam;
   const double c = A.coef[0];
   const double d = A.coef[1];
-  const double e = d - c * c;
+  const T e = (T)(d - c * c);
   if (threadIdx.x == 0) {
-    zero[0] = 0.0;
-    zero[1] = 0.0;
+    zero[0] = (T)0;
+    zero[1] = (T)0;
   }
   for (int a = threadIdx.x; a < m; a += blockDim.x) sS[a] = KIND == 0 ? A.xi[a] * A.xi[a] : A.s[a];
   __syncthreads();
 
-  double x[VPT], r[VPT], p[VPT], sv[VPT], dpc[VPT], dinv[VPT], omt[VPT];
+  T x[VPT], r[VPT], p[VPT], sv[VPT], dpc[VPT], dinv[VPT], omt[VPT];
   uint32_t na[VPT][kRegSlots];
+  uint32_t rmask[VPT];  // bit q set: neighbour q lives in another CTA
   int xr0[VPT], xr1[VPT];
   bool own[VPT];
-  const uint32_t zaddr = mapa_u32(smem_u32(zero), (uint32_t)rank);
+  const uint32_t zaddr = smem_u32(zero);
   const uint32_t base0 = smem_u32(ub0);
 #pragma unroll
   for (int k = 0; k < VPT; ++k) {
     const int li = threadIdx.x + k * blockDim.x;
     own[k] = li < nloc;
     const int i = beg + (own[k] ? li : 0);
-    x[k] = r[k] = p[k] = sv[k] = 0.0;
-    dpc[k] = dinv[k] = omt[k] = 0.0;
+    x[k] = r[k] = p[k] = sv[k] = (T)0;
+    dpc[k] = dinv[k] = omt[k] = (T)0;
     xr0[k] = xr1[k] = 0;
+    rmask[k] = 0u;
 #pragma unroll
     for (int q = 0; q < kRegSlots; ++q) na[k][q] = zaddr;
     if (own[k]) {
@@ -349,107 +381,184 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_reg_kernel(const PcgArgs A
       for (int q = 0; q < kRegSlots; ++q) {
         if (q < L.K) {
           const int pk = L.nbrp[(size_t)q * L.n + i];
-          // a missing neighbour reads the zero word (offset cancelled by subtracting the buffer offsets below)
-          if (pk >= 0) na[k][q] = mapa_u32(base0 + (uint32_t)((pk & 0xFFFFFF) * sizeof(double)), (uint32_t)(pk >> 24));
+          // a missing neighbour reads the local zero word (no buffer offset is added to it)
+          if (pk >= 0) {
+            const uint32_t loc = base0 + (uint32_t)((pk & 0xFFFFFF) * sizeof(T));
+            const int owner = pk >> 24;
+            if (owner == rank) {
+              na[k][q] = loc;
+            } else {
+              na[k][q] = mapa_u32(loc, (uint32_t)owner);
+              rmask[k] |= 1u << q;
+            }
+          }
         }
       }
-      dpc[k] = L.diag[i] + c;
-      double dd = lam * (L.l2diag[i] + 2.0 * c * L.diag[i] + d);
+      dpc[k] = (T)(L.diag[i] + c);
+      double dd = A.lam * (L.l2diag[i] + 2.0 * c * L.diag[i] + d);
       if (KIND == 0) {
         double o = 0.0;
         for (int a = 0; a < m; ++a) o += (double)A.Om[i + (int64_t)a * A.ldo] * sS[a];
-        omt[k] = o;
+        omt[k] = (T)o;
         dd += o;
       } else {
         xr0[k] = A.X.xr_ptr[i];
         xr1[k] = A.X.xr_ptr[i + 1];
         for (int q = xr0[k]; q < xr1[k]; ++q) dd += A.X.xr_val[q] * A.X.xr_val[q] * sS[A.X.xr_col[q]];
       }
-      dinv[k] = dd > 0.0 ? 1.0 / dd : 1.0;
-      x[k] = A.x[i];
+      dinv[k] = (T)(dd > 0.0 ? 1.0 / dd : 1.0);
+      x[k] = (T)A.x[i];
     }
   }
 
   // neighbour sum of the buffer at byte offset `off` from ub0 (zero word for a missing neighbour)
-  auto nsum = [&](int k, uint32_t off) -> double {
-    double acc = 0.0;
+  // all six loads are issued before the first add (in-order issue would
+  // otherwise serialise their latencies); the sum order is fixed
+  auto nsum = [&](int k, uint32_t off) -> T {
+    T v[kRegSlots];
 #pragma unroll
     for (int q = 0; q < kRegSlots; ++q) {
       const uint32_t a = na[k][q];
-      acc += ld_dsm(a == zaddr ? a : a + off);
+      if ((rmask[k] >> q) & 1u)
+        v[q] = ld_dsm<T>(a + off);
+      else
+        v[q] = ld_sh<T>(a == zaddr ? a : a + off);
     }
-    return acc;
+    return ((v[0] + v[1]) + (v[2] + v[3])) + (v[4] + v[5]);
   };
   // v side: partial X^T of the buffer in shared memory
-  auto ypartial = [&](double* buf) {
+  // (float32 kernel: the X data term runs in float32 on float32 copies of X;
+  // ypart and sY then hold floats)
+  float* ypart_f = reinterpret_cast<float*>(ypart);
+  float* sY_f = reinterpret_cast<float*>(sY);
+  float* sSf = ypart_f + m;  // float copy of sS in the upper half of the ypart words
+  if (kF32)
+    for (int a = threadIdx.x; a < m; a += blockDim.x) sSf[a] = (float)sS[a];
+  auto ypartial = [&](T* buf) {
     if (KIND == 1) {
       const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
       for (int a = wid; a < m; a += nw) {
         const int p0 = A.X.lx_ptr[rank * m + a], p1 = A.X.lx_ptr[rank * m + a + 1];
-        double acc = 0.0;
-        for (int q = p0 + lane; q < p1; q += 32) acc += A.X.lx_val[q] * buf[A.X.lx_row[q]];
-        acc = warp_sum(acc);
-        if (lane == 0) ypart[a] = acc;
+        if constexpr (kF32) {
+          float acc = 0.f;
+          for (int q = p0 + lane; q < p1; q += 32) acc += A.X.lx_valf[q] * buf[A.X.lx_row[q]];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+          if (lane == 0) ypart_f[a] = acc;
+        } else {
+          double acc = 0.0;
+          for (int q = p0 + lane; q < p1; q += 32) acc += A.X.lx_val[q] * (double)buf[A.X.lx_row[q]];
+          acc = warp_sum(acc);
+          if (lane == 0) ypart[a] = acc;
+        }
       }
     }
   };
   auto gather = [&]() {
     if (KIND == 1) {
       for (int a = threadIdx.x; a < m; a += blockDim.x) {
-        double t = 0.0;
-        for (int rr = 0; rr < C; ++rr) t += cl.map_shared_rank(ypart, (unsigned)rr)[a];
-        sY[a] = sS[a] * t;
+        if constexpr (kF32) {
+          float pv[kMaxCluster];
+#pragma unroll
+          for (int rr = 0; rr < kMaxCluster; ++rr)
+            pv[rr] = rr < C ? cl.map_shared_rank(ypart_f, (unsigned)rr)[a] : 0.f;
+          float t = 0.f;
+#pragma unroll
+          for (int rr = 0; rr < kMaxCluster; ++rr) t += pv[rr];
+          sY_f[a] = sSf[a] * t;
+        } else {
+          double pv[kMaxCluster];
+#pragma unroll
+          for (int rr = 0; rr < kMaxCluster; ++rr) pv[rr] = rr < C ? cl.map_shared_rank(ypart, (unsigned)rr)[a] : 0.0;
+          double t = 0.0;
+#pragma unroll
+          for (int rr = 0; rr < kMaxCluster; ++rr) t += pv[rr];
+          sY[a] = sS[a] * t;
+        }
       }
       __syncthreads();
     }
   };
-  auto data = [&](int k, double ui) -> double {
+  auto data = [&](int k, T ui) -> T {
     if (KIND == 0) return omt[k] * ui;
-    double acc = 0.0;
-    for (int q = xr0[k]; q < xr1[k]; ++q) acc += A.X.xr_val[q] * sY[A.X.xr_col[q]];
-    return acc;
+    if constexpr (kF32) {
+      float acc = 0.f;
+      for (int q = xr0[k]; q < xr1[k]; ++q) acc += A.X.xr_valf[q] * sY_f[A.X.xr_col[q]];
+      return acc;
+    } else {
+      double acc = 0.0;
+      for (int q = xr0[k]; q < xr1[k]; ++q) acc += A.X.xr_val[q] * sY[A.X.xr_col[q]];
+      return (T)acc;
+    }
   };
 
   // r0 = b - A x0
-  double tt[VPT];
+  T tt[VPT];
 #pragma unroll
   for (int k = 0; k < VPT; ++k)
     if (own[k]) ub0[threadIdx.x + k * blockDim.x] = x[k];
   cl.sync();
 #pragma unroll
   for (int k = 0; k < VPT; ++k) {
-    tt[k] = own[k] ? dpc[k] * x[k] - nsum(k, 0) : 0.0;
+    tt[k] = own[k] ? dpc[k] * x[k] - nsum(k, 0) : (T)0;
     if (own[k]) tb[threadIdx.x + k * blockDim.x] = tt[k];
   }
   ypartial(ub0);
   cl.sync();
   gather();
-  {
+  double bb;
+  if constexpr (kF32) {
+    DF v1[1] = {DF{0.f, 0.f}};
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) {
+      if (!own[k]) continue;
+      const int i = beg + threadIdx.x + k * blockDim.x;
+      const T wi = lam * (dpc[k] * tt[k] - nsum(k, off_tb) + e * x[k]) + data(k, x[k]);
+      const float bi = (float)A.b[i];
+      r[k] = bi - wi;
+      v1[0] = df_add(v1[0], df_prod(bi, bi));
+    }
+    block_sum_df<1>(v1, reinterpret_cast<DF*>(scr), reinterpret_cast<DF*>(red));
+    cl.sync();
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      DF g{0.f, 0.f};
+      if (lane < C) g = cl.map_shared_rank(reinterpret_cast<DF*>(red), lane)[0];
+      g = warp_sum_df(g);
+      if (lane == 0) reinterpret_cast<DF*>(scal)[0] = g;
+    }
+    __syncthreads();
+    const DF b2 = reinterpret_cast<const DF*>(scal)[0];
+    bb = (double)b2.hi + (double)b2.lo;
+  } else {
     double v[1] = {0.0};
 #pragma unroll
     for (int k = 0; k < VPT; ++k) {
       if (!own[k]) continue;
       const int i = beg + threadIdx.x + k * blockDim.x;
-      const double wi = lam * (dpc[k] * tt[k] - nsum(k, off_tb) + e * x[k]) + data(k, x[k]);
+      const T wi = lam * (dpc[k] * tt[k] - nsum(k, off_tb) + e * x[k]) + data(k, x[k]);
       const double bi = A.b[i];
-      r[k] = bi - wi;
+      r[k] = (T)(bi - (double)wi);
       v[0] += bi * bi;
     }
     block_sum<1>(v, scr, red);
+    cl.sync();
+    cluster_sum<1>(cl, red, scal, C);
+    bb = scal[0];
   }
-  cl.sync();
-  cluster_sum<1>(cl, red, scal, C);
-  const double bb = scal[0];
   int it = 0, status = 0;
   double rho = 0.0;
+  DF rho_df{0.f, 0.f};
   if (bb > 0.0) {
     const double tol2 = A.tol * A.tol * bb;
+    const float tol2f = (float)tol2;
     double gam_prev = 1.0, alpha_prev = 1.0;  // used by thread 0 only
+    DF gam_prev_df{1.f, 0.f}, alpha_prev_df{1.f, 0.f};
     int cur = 1;
     for (;;) {
       const uint32_t off_ub = cur ? off_ub1 : 0u;
-      double* ub = cur ? ub1 : ub0;
-      double u[VPT];
+      T* ub = cur ? ub1 : ub0;
+      T u[VPT];
 #pragma unroll
       for (int k = 0; k < VPT; ++k) {
         u[k] = r[k] * dinv[k];
@@ -458,20 +567,76 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_reg_kernel(const PcgArgs A
       cl.sync();
 #pragma unroll
       for (int k = 0; k < VPT; ++k) {
-        tt[k] = own[k] ? dpc[k] * u[k] - nsum(k, off_ub) : 0.0;
+        tt[k] = own[k] ? dpc[k] * u[k] - nsum(k, off_ub) : (T)0;
         if (own[k]) tb[threadIdx.x + k * blockDim.x] = tt[k];
       }
       ypartial(ub);
       cl.sync();
       gather();
+      T w[VPT];
+#pragma unroll
+      for (int k = 0; k < VPT; ++k)
+        w[k] = own[k] ? lam * (dpc[k] * tt[k] - nsum(k, off_tb) + e * u[k]) + data(k, u[k]) : (T)0;
+      if constexpr (kF32) {
+        // inner products from exact float products, summed in double-float
+        DF v3[3] = {DF{0.f, 0.f}, DF{0.f, 0.f}, DF{0.f, 0.f}};
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+          v3[0] = df_add(v3[0], df_prod(r[k], u[k]));
+          v3[1] = df_add(v3[1], df_prod(u[k], w[k]));
+          v3[2] = df_add(v3[2], df_prod(r[k], r[k]));
+        }
+        block_sum_df<3>(v3, reinterpret_cast<DF*>(scr), reinterpret_cast<DF*>(red));
+        cl.sync();
+        if (threadIdx.x < 32) {
+          const int lane = threadIdx.x;
+          DF g{0.f, 0.f}, dl{0.f, 0.f}, rh{0.f, 0.f};
+          if (lane < C) {
+            const DF* rr = cl.map_shared_rank(reinterpret_cast<DF*>(red), lane);
+            g = rr[0];
+            dl = rr[1];
+            rh = rr[2];
+          }
+          g = warp_sum_df(g);
+          dl = warp_sum_df(dl);
+          rh = warp_sum_df(rh);
+          if (lane == 0) {
+            float flag = 0.f;
+            DF alpha{0.f, 0.f}, beta{0.f, 0.f};
+            if (rh.hi <= tol2f) {
+              flag = 1.f;
+            } else if (it >= A.maxit) {
+              flag = 2.f;
+            } else {
+              DF den = dl;
+              if (it > 0) {
+                beta = df_div(g, gam_prev_df);
+                den = df_sub(dl, df_div(df_mul(beta, g), alpha_prev_df));
+              }
+              if (!(den.hi > 0.f) || !isfinite(den.hi)) {
+                flag = 3.f;
+              } else {
+                alpha = df_div(g, den);
+                gam_prev_df = g;
+                alpha_prev_df = alpha;
+              }
+            }
+            float* sf = reinterpret_cast<float*>(scal);
+            sf[0] = flag;
+            sf[1] = alpha.hi;
+            sf[2] = beta.hi;
+            sf[3] = rh.hi;
+            sf[4] = rh.lo;
+          }
+        }
+        __syncthreads();
+      } else {
       double v[3] = {0.0, 0.0, 0.0};
-      double w[VPT];
 #pragma unroll
       for (int k = 0; k < VPT; ++k) {
-        w[k] = own[k] ? lam * (dpc[k] * tt[k] - nsum(k, off_tb) + e * u[k]) + data(k, u[k]) : 0.0;
-        v[0] += r[k] * u[k];
-        v[1] += u[k] * w[k];
-        v[2] += r[k] * r[k];
+        v[0] += (double)(r[k] * u[k]);
+        v[1] += (double)(u[k] * w[k]);
+        v[2] += (double)(r[k] * r[k]);
       }
       block_sum<3>(v, scr, red);
       cl.sync();
@@ -489,6 +654,8 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_reg_kernel(const PcgArgs A
         dl = warp_sum(dl);
         rh = warp_sum(rh);
         if (lane == 0) {
+          // gam_prev / alpha_prev hold 1/gamma_{i-1} and 1/alpha_{i-1}: one
+          // division on the dependent chain (1/gamma_i is formed alongside)
           double flag = 0.0, alpha = 0.0, beta = 0.0;
           if (rh <= tol2) {
             flag = 1.0;
@@ -497,15 +664,15 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_reg_kernel(const PcgArgs A
           } else {
             double den = dl;
             if (it > 0) {
-              beta = g / gam_prev;
-              den = dl - beta * g / alpha_prev;
+              beta = g * gam_prev;
+              den = dl - beta * g * alpha_prev;
             }
             if (!(den > 0.0) || !isfinite(den)) {
               flag = 3.0;
             } else {
               alpha = g / den;
-              gam_prev = g;
-              alpha_prev = alpha;
+              gam_prev = 1.0 / g;
+              alpha_prev = den * gam_prev;
             }
           }
           scal[0] = flag;
@@ -515,8 +682,21 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_reg_kernel(const PcgArgs A
         }
       }
       __syncthreads();
-      const double flag = scal[0];
-      rho = scal[3];
+      }
+      double flag;
+      T alpha, beta;
+      if constexpr (kF32) {
+        const float* sf = reinterpret_cast<const float*>(scal);
+        flag = sf[0];
+        alpha = sf[1];
+        beta = sf[2];
+        rho_df = DF{sf[3], sf[4]};
+      } else {
+        flag = scal[0];
+        rho = scal[3];
+        alpha = (T)scal[1];
+        beta = (T)scal[2];
+      }
       if (flag == 1.0) break;
       if (flag == 2.0) {
         status = 1;
@@ -526,7 +706,6 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_reg_kernel(const PcgArgs A
         status = 2;
         break;
       }
-      const double alpha = scal[1], beta = scal[2];
 #pragma unroll
       for (int k = 0; k < VPT; ++k) {
         p[k] = it == 0 ? u[k] : u[k] + beta * p[k];
@@ -540,9 +719,10 @@ __global__ void __launch_bounds__(kPcgThreads, 1) pcg_reg_kernel(const PcgArgs A
   }
 #pragma unroll
   for (int k = 0; k < VPT; ++k)
-    if (own[k]) A.x[beg + threadIdx.x + k * blockDim.x] = x[k];
+    if (own[k]) A.x[beg + threadIdx.x + k * blockDim.x] = (double)x[k];
   cl.sync();  // no CTA leaves while another can still read its shared memory
   if (rank == 0 && threadIdx.x == 0) {
+    if constexpr (kF32) rho = (double)rho_df.hi + (double)rho_df.lo;
     A.stat->iters = it;
     A.stat->status = status;
     A.stat->relres = bb > 0.0 ? sqrt(rho / bb) : 0.0;
@@ -568,10 +748,11 @@ __global__ void lap_apply_kernel(const DevLap L, const double* __restrict__ x, d
 size_t pcg_smem_bytes(int chunk, int m) { return sizeof(double) * (3 * (size_t)chunk + 8 + 3 * (size_t)m + 128 + 8 + 2); }
 
 // Register-resident variant usable for this operator?  Returns VPT (0 = no).
-int pcg_reg_vpt(const DevLap& L) {
+int pcg_reg_vpt(const DevLap& L, bool fp32) {
   if (L.offw != nullptr || L.K > kRegSlots) return 0;
   if (L.chunk <= kPcgThreads) return 1;
   if (L.chunk <= 2 * kPcgThreads) return 2;
+  if (fp32 && L.chunk <= 4 * kPcgThreads) return 4;
   return 0;
 }
 
@@ -579,10 +760,14 @@ cudaError_t pcg_prepare(int /*data_kind*/, int csize, size_t /*smem_bytes*/) {
   // the attribute is per kernel, shared by the x and y grids: allow the maximum
   const size_t smem_bytes = 227 * 1024;
   cudaError_t e;
-  const void* fns[6] = {(const void*)pcg_cluster_kernel<0>, (const void*)pcg_cluster_kernel<1>,
-                        (const void*)pcg_reg_kernel<0, 1>,  (const void*)pcg_reg_kernel<1, 1>,
-                        (const void*)pcg_reg_kernel<0, 2>,  (const void*)pcg_reg_kernel<1, 2>};
-  for (int kind = 0; kind < 6; ++kind) {
+  const void* fns[14] = {(const void*)pcg_cluster_kernel<0>,         (const void*)pcg_cluster_kernel<1>,
+                         (const void*)pcg_reg_kernel<0, 1, double>, (const void*)pcg_reg_kernel<1, 1, double>,
+                         (const void*)pcg_reg_kernel<0, 2, double>, (const void*)pcg_reg_kernel<1, 2, double>,
+                         (const void*)pcg_reg_kernel<0, 1, float>,  (const void*)pcg_reg_kernel<1, 1, float>,
+                         (const void*)pcg_reg_kernel<0, 2, float>,  (const void*)pcg_reg_kernel<1, 2, float>,
+                         (const void*)pcg_reg_kernel<0, 4, float>,  (const void*)pcg_reg_kernel<1, 4, float>,
+                         (const void*)pcg_reg_kernel<0, 4, float>,  (const void*)pcg_reg_kernel<1, 4, float>};
+  for (int kind = 0; kind < 14; ++kind) {
     const void* fn = fns[kind];
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
     if (e != cudaSuccess) return e;
@@ -635,14 +820,23 @@ cudaError_t pcg_launch(const PcgArgs& a, int data_kind, cudaStream_t st) {
   cfg.attrs = at;
   cfg.numAttrs = 1;
   count_launch();
-  const int vpt = a.force_generic ? 0 : pcg_reg_vpt(a.L);
+  const bool f32 = a.fp32 != 0;
+  const int vpt = a.force_generic ? 0 : pcg_reg_vpt(a.L, f32);
+  if (f32) {
+    if (vpt == 1) return data_kind == 0 ? cudaLaunchKernelEx(&cfg, pcg_reg_kernel<0, 1, float>, a)
+                                        : cudaLaunchKernelEx(&cfg, pcg_reg_kernel<1, 1, float>, a);
+    if (vpt == 2) return data_kind == 0 ? cudaLaunchKernelEx(&cfg, pcg_reg_kernel<0, 2, float>, a)
+                                        : cudaLaunchKernelEx(&cfg, pcg_reg_kernel<1, 2, float>, a);
+    if (vpt == 4) return data_kind == 0 ? cudaLaunchKernelEx(&cfg, pcg_reg_kernel<0, 4, float>, a)
+                                        : cudaLaunchKernelEx(&cfg, pcg_reg_kernel<1, 4, float>, a);
+  }
   if (vpt == 1) {
-    if (data_kind == 0) return cudaLaunchKernelEx(&cfg, pcg_reg_kernel<0, 1>, a);
-    return cudaLaunchKernelEx(&cfg, pcg_reg_kernel<1, 1>, a);
+    if (data_kind == 0) return cudaLaunchKernelEx(&cfg, pcg_reg_kernel<0, 1, double>, a);
+    return cudaLaunchKernelEx(&cfg, pcg_reg_kernel<1, 1, double>, a);
   }
   if (vpt == 2) {
-    if (data_kind == 0) return cudaLaunchKernelEx(&cfg, pcg_reg_kernel<0, 2>, a);
-    return cudaLaunchKernelEx(&cfg, pcg_reg_kernel<1, 2>, a);
+    if (data_kind == 0) return cudaLaunchKernelEx(&cfg, pcg_reg_kernel<0, 2, double>, a);
+    return cudaLaunchKernelEx(&cfg, pcg_reg_kernel<1, 2, double>, a);
   }
   if (data_kind == 0) return cudaLaunchKernelEx(&cfg, pcg_cluster_kernel<0>, a);
   return cudaLaunchKernelEx(&cfg, pcg_cluster_kernel<1>, a);

@@ -312,3 +312,32 @@ void precond_dots(int j, const double* R, const double* Dg, int64_t ld, double* 
 }
 
 }  // namespace cr
+
+namespace cr {
+namespace {
+__global__ void to_f32_kernel(int64_t n, const double* __restrict__ x, float* __restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (float)x[i];
+}
+__global__ void add_f32_kernel(int r, int c, const float* __restrict__ x, int64_t ldx, double* __restrict__ y,
+                               int64_t ldy) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)r * c) return;
+  const int64_t i = t % r, l = t / r;
+  y[i + l * ldy] += (double)x[i + l * ldx];
+}
+}  // namespace
+
+void to_f32(int64_t n, const double* x, float* y, cudaStream_t st) {
+  if (n <= 0) return;
+  count_launch();
+  to_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, y);
+}
+
+void add_f32(int r, int c, const float* x, int64_t ldx, double* y, int64_t ldy, cudaStream_t st) {
+  const int64_t tot = (int64_t)r * c;
+  if (tot <= 0) return;
+  count_launch();
+  add_f32_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(r, c, x, ldx, y, ldy);
+}
+}  // namespace cr
