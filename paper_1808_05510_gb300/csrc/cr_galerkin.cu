@@ -491,6 +491,9 @@ __device__ __forceinline__ void gather_blocks(cgc::cluster_group& cl, float* buf
 }
 
 __global__ void __launch_bounds__(kClThreads, 1) galerkin_cluster_f32_kernel(const GalClArgs a) {
+  // Chronopoulos-Gear form of the Jacobi-preconditioned matrix CG: one
+  // operator application (on U = D^-1 R) and one fused reduction of
+  // <R, U>, <U, W>, <R, R> per iteration.
   cgc::cluster_group cl = cgc::this_cluster();
   const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
@@ -499,72 +502,42 @@ __global__ void __launch_bounds__(kClThreads, 1) galerkin_cluster_f32_kernel(con
   const int c0 = min(j, rank * cw), c1 = min(j, c0 + cw), nc = c1 - c0;
   const int a0 = min(m, rank * aw), a1 = min(m, a0 + aw), na = a1 - a0;
   extern __shared__ __align__(16) float fsm[];
-  float* Xf = fsm;                 // j x j (ld j): full search direction
+  float* Xf = fsm;                 // j x j (ld j): full copy of U
   float* Gwf = Xf + j * j;         // j x m (ld j)
   float* Zo = Gwf + j * m;         // own blocks, j x cw each (ld j)
   float* Ro = Zo + j * cw;
-  float* zo = Ro + j * cw;
-  float* Qo = zo + j * cw;
-  float* T1o = Qo + j * cw;
+  float* Po = Ro + j * cw;
+  float* So = Po + j * cw;
+  float* Wo = So + j * cw;
+  float* T1o = Wo + j * cw;
   float* T2o = T1o + j * cw;
-  float* THo = T2o + j * cw;       // j x aw
+  float* Dio = T2o + j * cw;       // 1 / diag(K) on own columns
+  float* THo = Dio + j * cw;       // j x aw
   DF* scr = reinterpret_cast<DF*>(THo + j * aw);  // [32]
-  DF* red = scr + 32;              // [2][4]
-  float* scal = reinterpret_cast<float*>(red + 8);  // [8]
-  float* Xo = Xf + (int64_t)c0 * j;  // own columns of X inside the full copy
+  DF* red = scr + 32;              // [4]
+  float* scal = reinterpret_cast<float*>(red + 4);  // [8]
+  float* Uo = Xf + (int64_t)c0 * j;  // own columns of U inside the full copy
   const int tid = threadIdx.x, nth = blockDim.x;
   const float lam = a.lam, lam2 = 2.f * a.lam;
 
-  // init: Z = 0, R = F, z = R / D, P = z
-  DF rz{0.f, 0.f}, rr{0.f, 0.f};
+  // Z = 0, R = F, U = D^-1 R
   for (int t = tid; t < j * nc; t += nth) {
     const int i = t % j, lc = t / j;
     const int64_t o = i + (int64_t)(c0 + lc) * ld;
-    const float r = a.F[o], z = r / a.Dg[o];
+    const float r = a.F[o], di = 1.f / a.Dg[o];
     Zo[t] = 0.f;
     Ro[t] = r;
-    zo[t] = z;
-    Xo[t] = z;
-    rz = df_add(rz, df_prod(r, z));
-    rr = df_add(rr, df_prod(r, r));
+    Dio[t] = di;
+    Uo[t] = r * di;
+    Po[t] = 0.f;
+    So[t] = 0.f;
   }
-  {
-    const DF s0 = cl_block_df(rz, scr);
-    const DF s1 = cl_block_df(rr, scr);
-    if (tid == 0) {
-      red[0] = s0;
-      red[1] = s1;
-    }
-  }
-  cl.sync();
-  if (tid < 32) {
-    DF g{0.f, 0.f}, h{0.f, 0.f};
-    if (tid < C) {
-      const DF* rm = cl.map_shared_rank(red, tid);
-      g = rm[0];
-      h = rm[1];
-    }
-    g = warp_sum_df(g);
-    h = warp_sum_df(h);
-    if (tid == 0) {
-      reinterpret_cast<DF*>(scal)[0] = g;
-      reinterpret_cast<DF*>(scal)[1] = h;
-    }
-  }
-  __syncthreads();
-  DF rho = reinterpret_cast<DF*>(scal)[0];
-  DF rrt = reinterpret_cast<DF*>(scal)[1];
   int it = 0, status = 0;
-  while (rrt.hi > a.tol2) {
-    if (it >= a.maxit) {
-      status = 1;
-      break;
-    }
-    cl.sync();  // B1: own columns of X published
-    // all-gather X: copy the other CTAs' column blocks
+  DF gam_prev{1.f, 0.f}, alpha_prev{1.f, 0.f}, rrt{0.f, 0.f};
+  for (;;) {
+    cl.sync();  // B1: own columns of U published
     gather_blocks(cl, Xf, j * j, j * cw, rank);
     __syncthreads();
-    // T2, T1 on own columns; TH on own injections
     for (int t = tid; t < j * nc; t += nth) {
       const int i = t % j, lc = t / j;
       const float* b2 = a.B2 + (int64_t)(c0 + lc) * ld;
@@ -596,85 +569,96 @@ __global__ void __launch_bounds__(kClThreads, 1) galerkin_cluster_f32_kernel(con
     cl.sync();  // B2: own columns of Gw published
     gather_blocks(cl, Gwf, j * m, j * aw, rank);
     __syncthreads();
-    // Q on own columns and <X, Q>
-    DF pq{0.f, 0.f};
+    // W = K(U) on own columns; partial <R, U>, <U, W>, <R, R>
+    DF v0{0.f, 0.f}, v1{0.f, 0.f}, v2{0.f, 0.f};
     for (int t = tid; t < j * nc; t += nth) {
       const int i = t % j, lc = t / j;
       const int l = c0 + lc;
       float s1 = 0.f, s2 = 0.f, s3 = 0.f;
       for (int k = 0; k < j; ++k) {
         s1 = fmaf(__ldg(a.A1 + i + (int64_t)k * ld), T1o[k + lc * j], s1);
-        s2 = fmaf(__ldg(a.A2 + i + (int64_t)k * ld), Xo[k + lc * j], s2);
+        s2 = fmaf(__ldg(a.A2 + i + (int64_t)k * ld), Uo[k + lc * j], s2);
       }
       for (int al = 0; al < m; ++al) s3 = fmaf(Gwf[i + al * j], __ldg(a.H + l + (int64_t)al * ld), s3);
-      const float q = lam * T2o[t] + lam2 * s1 + lam * s2 + s3;
-      Qo[t] = q;
-      pq = df_add(pq, df_prod(Xo[t], q));
+      const float w = lam * T2o[t] + lam2 * s1 + lam * s2 + s3;
+      Wo[t] = w;
+      const float u = Uo[t], r = Ro[t];
+      v0 = df_add(v0, df_prod(r, u));
+      v1 = df_add(v1, df_prod(u, w));
+      v2 = df_add(v2, df_prod(r, r));
     }
     {
-      const DF s = cl_block_df(pq, scr);
-      if (tid == 0) red[2] = s;
+      const DF s0 = cl_block_df(v0, scr);
+      const DF s1 = cl_block_df(v1, scr);
+      const DF s2 = cl_block_df(v2, scr);
+      if (tid == 0) {
+        red[0] = s0;
+        red[1] = s1;
+        red[2] = s2;
+      }
     }
     cl.sync();  // B3
     if (tid < 32) {
-      DF g{0.f, 0.f};
-      if (tid < C) g = cl.map_shared_rank(red, tid)[2];
+      DF g{0.f, 0.f}, dl{0.f, 0.f}, rh{0.f, 0.f};
+      if (tid < C) {
+        const DF* rm = cl.map_shared_rank(red, tid);
+        g = rm[0];
+        dl = rm[1];
+        rh = rm[2];
+      }
       g = warp_sum_df(g);
+      dl = warp_sum_df(dl);
+      rh = warp_sum_df(rh);
       if (tid == 0) {
-        float ok = (g.hi > 0.f && isfinite(g.hi)) ? 1.f : 0.f;
-        const DF alpha = ok > 0.f ? df_div(rho, g) : DF{0.f, 0.f};
-        scal[4] = ok;
-        scal[5] = alpha.hi;
+        float flag = 0.f;
+        DF alpha{0.f, 0.f}, beta{0.f, 0.f};
+        if (rh.hi <= a.tol2) {
+          flag = 1.f;
+        } else if (it >= a.maxit) {
+          flag = 2.f;
+        } else {
+          DF den = dl;
+          if (it > 0) {
+            beta = df_div(g, gam_prev);
+            den = df_sub(dl, df_div(df_mul(beta, g), alpha_prev));
+          }
+          if (!(den.hi > 0.f) || !isfinite(den.hi)) {
+            flag = 3.f;
+          } else {
+            alpha = df_div(g, den);
+            gam_prev = g;
+            alpha_prev = alpha;
+          }
+        }
+        scal[0] = flag;
+        scal[1] = alpha.hi;
+        scal[2] = beta.hi;
+        reinterpret_cast<DF*>(scal)[2] = rh;
       }
     }
     __syncthreads();
-    if (scal[4] == 0.f) {
+    const float flag = scal[0];
+    rrt = reinterpret_cast<DF*>(scal)[2];
+    if (flag == 1.f) break;
+    if (flag == 2.f) {
+      status = 1;
+      break;
+    }
+    if (flag == 3.f) {
       status = 2;
       break;
     }
-    const float alpha = scal[5];
-    DF rz2{0.f, 0.f}, rr2{0.f, 0.f};
+    const float alpha = scal[1], beta = scal[2];
     for (int t = tid; t < j * nc; t += nth) {
-      const int i = t % j, lc = t / j;
-      const int64_t o = i + (int64_t)(c0 + lc) * ld;
-      Zo[t] = fmaf(alpha, Xo[t], Zo[t]);
-      const float r = fmaf(-alpha, Qo[t], Ro[t]);
+      const float p = fmaf(beta, Po[t], Uo[t]);
+      const float s = fmaf(beta, So[t], Wo[t]);
+      Po[t] = p;
+      So[t] = s;
+      Zo[t] = fmaf(alpha, p, Zo[t]);
+      const float r = fmaf(-alpha, s, Ro[t]);
       Ro[t] = r;
-      const float z = r / a.Dg[o];
-      zo[t] = z;
-      rz2 = df_add(rz2, df_prod(r, z));
-      rr2 = df_add(rr2, df_prod(r, r));
+      Uo[t] = r * Dio[t];
     }
-    {
-      const DF s0 = cl_block_df(rz2, scr);
-      const DF s1 = cl_block_df(rr2, scr);
-      if (tid == 0) {
-        red[4] = s0;
-        red[5] = s1;
-      }
-    }
-    cl.sync();  // B4
-    if (tid < 32) {
-      DF g{0.f, 0.f}, h{0.f, 0.f};
-      if (tid < C) {
-        const DF* rm = cl.map_shared_rank(red, tid);
-        g = rm[4];
-        h = rm[5];
-      }
-      g = warp_sum_df(g);
-      h = warp_sum_df(h);
-      if (tid == 0) {
-        const DF beta = rho.hi > 0.f ? df_div(g, rho) : DF{0.f, 0.f};
-        reinterpret_cast<DF*>(scal)[0] = g;
-        reinterpret_cast<DF*>(scal)[1] = h;
-        scal[6] = beta.hi;
-      }
-    }
-    __syncthreads();
-    rho = reinterpret_cast<DF*>(scal)[0];
-    rrt = reinterpret_cast<DF*>(scal)[1];
-    const float beta = scal[6];
-    for (int t = tid; t < j * nc; t += nth) Xo[t] = fmaf(beta, Xo[t], zo[t]);
     ++it;
   }
   for (int t = tid; t < j * nc; t += nth) {
@@ -690,7 +674,7 @@ __global__ void __launch_bounds__(kClThreads, 1) galerkin_cluster_f32_kernel(con
 }
 
 size_t gal_cl_smem(int j, int m, int cw, int aw) {
-  return sizeof(float) * ((size_t)j * j + (size_t)j * m + 7 * (size_t)j * cw + (size_t)j * aw) + sizeof(DF) * 40 +
+  return sizeof(float) * ((size_t)j * j + (size_t)j * m + 9 * (size_t)j * cw + (size_t)j * aw) + sizeof(DF) * 40 +
          sizeof(float) * 8 + 64;
 }
 
