@@ -128,6 +128,25 @@ def peaks():
         return 6800.0, "of fallback"
 
 
+def pcg_traffic(form: str):
+    """DRAM bytes per PCG launch from the committed ncu summary, or None when the
+    kernel source has changed since the counters were taken."""
+    import hashlib
+
+    try:
+        with open(os.path.join(ROOT, "profiles", "pcg_reg_kernel_traffic.json")) as f:
+            d = json.load(f)
+        with open(os.path.join(ROOT, "paper_1808_05510_gb300", "csrc", "cr_pcg.cu"), "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()[:16]
+        if h != d["source_sha256_16"]:
+            return None
+        b = d["dram_bytes_per_launch"]
+        pre = "fp64" if form == "fp64" else "f32"
+        return 0.5 * (b[pre + "_u"] + b[pre + "_v"])
+    except Exception:
+        return None
+
+
 def pcg_bytes_per_iter(n: int, slots: int = 6, word: float = 8.0) -> float:
     """Algorithmic bytes of one Chronopoulos-Gear PCG iteration: read and write
     r, x, p, s (8 words), read the Jacobi diagonal and the data diagonal (2
@@ -271,7 +290,8 @@ def run_ours(args, rank, world, local_rank):
     head = forms[args.precision]
     hbm, peak_kind = peaks()
     roofline = {"bound": "hbm", "achieved": head["pcg"]["achieved"], "peak": hbm, "unit": "GB/s",
-                "frac": head["pcg"]["achieved"] / hbm, "traffic": None, "kernel": "pcg_reg_kernel (cluster PCG)",
+                "frac": head["pcg"]["achieved"] / hbm, "traffic": pcg_traffic(args.precision),
+                "kernel": "pcg_reg_kernel (cluster PCG)",
                 "peak_kind": peak_kind, "pcg_share_of_step": head["pcg"]["share_of_step"],
                 "avg_launch_us": head["pcg"]["avg_launch_us"], "iters_per_launch": head["pcg"]["iters_per_launch"],
                 "us_per_iter": head["pcg"]["us_per_iter"]}

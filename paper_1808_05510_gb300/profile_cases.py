@@ -1,0 +1,50 @@
+"""Representative kernel cases for profiling runs (ncu) on the visual-cortex workload.
+
+    python -m paper_1808_05510_gb300.profile_cases pcg fp64|mixed
+        one u-side and one v-side ALS solve (Eqs. ALS_linsys, ALS_linsys_v) for the
+        first ALS vector v = R_0^T 1 / |R_0^T 1|, to relative residual 1e-8, twice
+    python -m paper_1808_05510_gb300.profile_cases galerkin fp64|mixed
+        two Galerkin projections (Eq. Proj_Sylv) at rank 60 from a float64 greedy run
+"""
+from __future__ import annotations
+
+import sys
+
+import numpy as np
+
+
+def pcg(form: str) -> None:
+    from . import synth
+    from .conreg import CR_FP64, CR_MIXED, ConReg
+
+    p = synth.visual_cortex()
+    prec = CR_MIXED if form == "mixed" else CR_FP64
+    with ConReg.from_problem(p, r_cap=4) as g0:
+        v = g0.cr_apply_residual(np.ones(p.ny), trans=True)
+        v /= np.linalg.norm(v)
+        rhs_u = g0.cr_apply_residual(v)
+        u = rhs_u / np.linalg.norm(rhs_u)
+        rhs_v = g0.cr_apply_residual(u, trans=True)
+    with ConReg.from_problem(p, r_cap=4, precision=prec, pcg_tol=1e-8) as g:
+        for _ in range(2):
+            print("iterations", g.cr_solve_u(v, rhs_u)[1], g.cr_solve_v(u, rhs_v)[1], flush=True)
+
+
+def galerkin(form: str) -> None:
+    from . import synth
+    from .conreg import CR_FP64, CR_MIXED, ConReg
+
+    p = synth.visual_cortex()
+    with ConReg.from_problem(p, r_cap=100) as g:
+        g.cr_solve(60, 1e-9, 0.0)
+        U, Z, V = g.cr_get_factors()
+    prec = CR_MIXED if form == "mixed" else CR_FP64
+    with ConReg.from_problem(p, r_cap=100, precision=prec) as g:
+        for k in range(2):
+            g.cr_set_factors(U, Z * (1.0 + 1e-3 * (k + 1)), V)
+            print(g.cr_project(5e-10), flush=True)
+
+
+if __name__ == "__main__":
+    case, form = sys.argv[1], (sys.argv[2] if len(sys.argv) > 2 else "fp64")
+    {"pcg": pcg, "galerkin": galerkin}[case](form)
