@@ -214,6 +214,14 @@ cr_status cr_solve_u(struct cr_problem* p, const double* v_host, const double* r
 cr_status cr_solve_v(struct cr_problem* p, const double* u_host, const double* rhs_host, double* v_hat_host,
                      int32_t* iters);
 
+/* Galerkin assembly G_a = U^T diag(Omega_a) U for every injection a (the
+ * coefficient matrices of the data term of Eq. Proj_Sylv) for the current U,
+ * as float32: method 0 = tensor cores (tcgen05, BF16 hi/lo split operands,
+ * float32 accumulation; needs r_cap <= 128), method 1 = the float64 matrices
+ * rounded to float32.  Copies G_a to G_host + a*ldg*j (j x j, leading
+ * dimension ldg >= j).  Mixed form only (CR_ESTATE otherwise). */
+cr_status cr_galerkin_assembly(struct cr_problem* p, int32_t method, float* G_host, int64_t ldg);
+
 /* Counters and (profile mode) per-phase device times; reset != 0 zeroes them
  * after reading.  Synchronises the problem's stream. */
 cr_status cr_get_stats(struct cr_problem* p, cr_stats* s, int32_t reset);

@@ -92,6 +92,7 @@ SIGNATURES = {
     "cr_solve_u": (C.c_int, [C.c_void_p, _dp, _dp, _dp, _ip]),
     "cr_solve_v": (C.c_int, [C.c_void_p, _dp, _dp, _dp, _ip]),
     "cr_get_stats": (C.c_int, [C.c_void_p, C.POINTER(cr_stats), C.c_int32]),
+    "cr_galerkin_assembly": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_float), C.c_int64]),
     "cr_solve_u_noalloc": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_double,
                                      C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int32, _ip,
                                      C.c_void_p]),
@@ -297,6 +298,18 @@ class ConReg:
         out = np.zeros(self.nx if trans else self.ny)
         _check(self._lib.cr_apply_residual(self.h, int(trans), _ptr(vec), _ptr(out)), self.h, "cr_apply_residual")
         return out
+
+    def cr_galerkin_assembly(self, method: int = 0) -> np.ndarray:
+        """G[a] = U^T diag(Omega_a) U (float32) for the current U; method 0 tensor cores, 1 float64 rounded."""
+        j = self.cr_get_rank()
+        G = np.zeros((self.m, j, j), dtype=np.float32)
+        if j:
+            # block a at a*j*j, column-major j x j
+            buf = np.zeros(self.m * j * j, dtype=np.float32)
+            _check(self._lib.cr_galerkin_assembly(self.h, int(method), buf.ctypes.data_as(C.POINTER(C.c_float)), j),
+                   self.h, "cr_galerkin_assembly")
+            G = buf.reshape(self.m, j, j).transpose(0, 2, 1).copy()
+        return G
 
     def cr_get_stats(self, reset: bool = False) -> dict:
         s = cr_stats()

@@ -87,6 +87,12 @@ struct cr_problem {
   int* gerr = nullptr;
   int gal_nb = 0;
   // float32 copies for the mixed form's inner Galerkin CG
+  // BF16 hi/lo shadows of U (n_y x 128, column stride ldb) for the tensor-core assembly
+  void *ubhi = nullptr, *ublo = nullptr;
+  int64_t ldb = 0;
+  int tc_splits = 0;
+  float* tcpart = nullptr;
+  int* tcerr = nullptr;
   float *fA1 = nullptr, *fA2 = nullptr, *fB1 = nullptr, *fB2 = nullptr, *fDg = nullptr, *fH = nullptr,
         *fG = nullptr, *fF = nullptr, *fZ = nullptr, *fR = nullptr, *fPa = nullptr, *fPb = nullptr, *fQ = nullptr,
         *fT2 = nullptr, *fT1 = nullptr, *fTH = nullptr, *fGw = nullptr, *fzb = nullptr;
@@ -591,6 +597,9 @@ cr_status grow_projections(cr_problem* p, int q) {
   double* vq = p->VV + (size_t)3 * q * nx;
   lap_apply(p->Ly, uq, uq + ny, 0.0, st);
   lap_apply(p->Ly, uq + ny, uq + 2 * ny, 0.0, st);
+  if (p->ubhi && q < 128)
+    bf16_split(ny, 1, uq, ny, (uint16_t*)p->ubhi + (size_t)q * p->ldb, (uint16_t*)p->ublo + (size_t)q * p->ldb, p->ldb,
+               st);
   lap_apply(p->Lx, vq, vq + nx, 0.0, st);
   lap_apply(p->Lx, vq + nx, vq + 2 * nx, 0.0, st);
   const int64_t ldu = 3 * (int64_t)ny, ldv = 3 * (int64_t)nx;
@@ -617,10 +626,23 @@ cr_status grow_projections(cr_problem* p, int q) {
 // K (the paper's CG is unpreconditioned; the iterate it converges to is the
 // same Galerkin solution).  Device scalars: gs[k & 1] = <R_k, D^-1 R_k>,
 // gs[2] = <P, K P>, gs[3] = |F|^2, gs[4] = |R|^2.
-// float32 G_a = U^T diag(Omega_a) U for the inner solves of the mixed form.
-void mixed_G(cr_problem* p) {
+// float32 G_a = U^T diag(Omega_a) U for the inner solves of the mixed form:
+// re-assembled on the tensor cores from the BF16 shadows of U when j <= 128,
+// else converted from the float64 G that the projections maintain.
+cr_status mixed_G(cr_problem* p, bool force_f64 = false) {
   const int64_t ld = p->rcap;
+  if (!force_f64 && p->ubhi && p->j <= 128) {
+    const cudaError_t e = galerkin_assemble_tc(p->ny, p->j, p->m, p->ubhi, p->ublo, p->ldb, p->Om, p->ny, p->tc_splits,
+                                               p->tcpart, p->fG, ld, p->tcerr, p->st);
+    if (e == cudaSuccess) return CR_OK;
+    if (e != cudaErrorNotSupported) {
+      p->err = std::string("tensor-core Galerkin assembly failed: ") + cudaGetErrorString(e);
+      return CR_ECUDA;
+    }
+    cudaGetLastError();
+  }
   to_f32(ld * ld * p->m, p->G, p->fG, p->st);
+  return CR_OK;
 }
 
 cr_status do_project(cr_problem* p, double tol, cr_proj_info* info) {
@@ -653,7 +675,7 @@ cr_status do_project(cr_problem* p, double tol, cr_proj_info* info) {
     to_f32(r2, p->B2, p->fB2, st);
     to_f32(r2, p->gDg, p->fDg, st);
     to_f32(ld * p->m, p->H, p->fH, st);
-    mixed_G(p);
+    TRY(mixed_G(p));
     for (int outer = 0; outer < 40 && fn2 > 0.0; ++outer) {
       galerkin_apply(p, p->Z, p->gQ);
       mat_axpby(j, j, 1.0, p->F, ld, -1.0, p->gQ, ld, p->gR, ld, st);
@@ -1200,6 +1222,17 @@ cr_status cr_create(const cr_problem_desc* d, const cr_options* o, cr_problem** 
       CK(dalloc(p, b, r2));
     for (float** b : {&p->fH, &p->fTH, &p->fGw}) CK(dalloc(p, b, (size_t)rc * m));
     CK(dalloc(p, &p->fG, r2 * m));
+    if (rc <= 128) {
+      p->ldb = ((int64_t)ny + 63) / 64 * 64;
+      uint16_t *h16 = nullptr, *l16 = nullptr;
+      CK(dalloc(p, &h16, (size_t)p->ldb * 128));
+      CK(dalloc(p, &l16, (size_t)p->ldb * 128));
+      p->ubhi = h16;
+      p->ublo = l16;
+      p->tc_splits = std::max(1, std::min((int)((ny + 63) / 64), (2 * 152 + (int)m - 1) / (int)m));
+      CK(dalloc(p, &p->tcpart, tc_part_elems(p->tc_splits, (int)m)));
+      CK(dalloc(p, &p->tcerr, 1));
+    }
   }
   CK(dalloc(p, &p->stat, 2));
   CK(dalloc(p, &p->ds, DS_COUNT));
@@ -1309,6 +1342,27 @@ cr_status cr_residual(cr_problem* p, double* relres, double* J, double* dW) {
   }
   if (relres) TRY(do_relres(p, relres));
   prof_end(p, CR_PHASE_RESID);
+  return CR_OK;
+}
+
+cr_status cr_galerkin_assembly(cr_problem* p, int32_t method, float* G_host, int64_t ldg) {
+  if (!p || !G_host) return CR_EINVAL;
+  const int j = p->j;
+  if (j == 0) return CR_OK;
+  if (ldg < j) return fail(p, CR_EINVAL, "ldg < rank");
+  if (!p->fG) return fail(p, CR_ESTATE, "the assembly runs in the mixed form (precision = CR_MIXED)");
+  if (method == 0 && !(p->ubhi && j <= 128)) return fail(p, CR_EINVAL, "tensor-core assembly needs r_cap <= 128");
+  if (p->tcerr) CUCHK(p, cudaMemsetAsync(p->tcerr, 0, sizeof(int), p->st));
+  TRY(mixed_G(p, method != 0));
+  int herr = 0;
+  if (p->tcerr) CUCHK(p, cudaMemcpyAsync(&herr, p->tcerr, sizeof(int), cudaMemcpyDeviceToHost, p->st));
+  const int64_t ld = p->rcap;
+  for (int a = 0; a < p->m; ++a)
+    CUCHK(p, cudaMemcpy2DAsync(G_host + (size_t)a * ldg * j, ldg * sizeof(float), p->fG + (size_t)a * ld * ld,
+                               ld * sizeof(float), j * sizeof(float), j, cudaMemcpyDeviceToHost, p->st));
+  p->d2h_bytes += (int64_t)sizeof(float) * p->m * j * j;
+  TRY(sync(p));
+  if (herr) return fail(p, CR_ETIMEOUT, "tensor-core assembly: an mbarrier wait timed out");
   return CR_OK;
 }
 

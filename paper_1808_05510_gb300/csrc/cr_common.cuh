@@ -161,6 +161,13 @@ cudaError_t galerkin_cluster_f32_launch(int j, int m, int64_t ld, double lam, co
                                         const float* F, const float* Dg, float* Z, double tol2, int maxit,
                                         double* out, cudaStream_t st);
 
+// ---------------------------------------------------------------- cr_tc.cu
+size_t tc_part_elems(int splits, int m);
+void bf16_split(int n, int cols, const double* U, int64_t ldu, void* hi, void* lo, int64_t ldb, cudaStream_t st);
+cudaError_t galerkin_assemble_tc(int n, int j, int m, const void* hi, const void* lo, int64_t ldb, const uint8_t* Om,
+                                 int64_t ldo, int splits, float* part, float* G, int64_t ld, int* err,
+                                 cudaStream_t st);
+
 }  // namespace cr
 
 namespace cr {

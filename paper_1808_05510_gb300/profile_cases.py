@@ -5,6 +5,8 @@
         first ALS vector v = R_0^T 1 / |R_0^T 1|, to relative residual 1e-8, twice
     python -m paper_1808_05510_gb300.profile_cases galerkin fp64|mixed
         two Galerkin projections (Eq. Proj_Sylv) at rank 60 from a float64 greedy run
+    python -m paper_1808_05510_gb300.profile_cases assembly tc
+        three tensor-core assemblies of G_a = U^T diag(Omega_a) U at rank 100
 """
 from __future__ import annotations
 
@@ -45,6 +47,23 @@ def galerkin(form: str) -> None:
             print(g.cr_project(5e-10), flush=True)
 
 
+def assembly(form: str) -> None:
+    """Tensor-core Galerkin assembly at rank 100 (random orthonormal U), three times."""
+    from . import synth
+    from .conreg import CR_MIXED, ConReg
+
+    p = synth.visual_cortex()
+    j = 100
+    rng = np.random.default_rng(7)
+    U, _ = np.linalg.qr(rng.standard_normal((p.ny, j)))
+    V, _ = np.linalg.qr(rng.standard_normal((p.nx, j)))
+    with ConReg.from_problem(p, r_cap=j, precision=CR_MIXED) as g:
+        g.cr_set_factors(U, np.eye(j), V)
+        for _ in range(3):
+            G = g.cr_galerkin_assembly(0 if form != "fp64" else 1)
+        print("assembled", G.shape, flush=True)
+
+
 if __name__ == "__main__":
     case, form = sys.argv[1], (sys.argv[2] if len(sys.argv) > 2 else "fp64")
-    {"pcg": pcg, "galerkin": galerkin}[case](form)
+    {"pcg": pcg, "galerkin": galerkin, "assembly": assembly}[case](form)
