@@ -251,6 +251,47 @@ cr_status cr_solve_u_noalloc(int64_t n, const int32_t* rowptr_dev, const int32_t
                              double lambda, double c, double d, const double* omega_dev, const double* rhs_dev,
                              double* u_hat_dev, double tol, int32_t maxit, int32_t* iters, void* stream);
 
+/* ---- learned preconditioner (the paper has no counterpart: its sub-problems
+ * are solved directly) ------------------------------------------------------
+ * A 4-layer 3x3x3 convolutional network on the voxel box (channels 2 -> 16 ->
+ * 16 -> 16 -> 1, zero padding, ReLU between layers; BF16 weights and
+ * activations, float32 accumulation).  Input channel 0 is the Jacobi-scaled
+ * residual D^-1 r / s on the mask voxels (s = |D^-1 r|), channel 1 the mask;
+ * the preconditioner is z = D^-1 r + s net(input), used by a flexible CG
+ * (Polak-Ribiere) in place of Jacobi-PCG when cr_options.precond =
+ * CR_PRECOND_LEARNED.  Device buffers are float32, layout [batch][channel][z][y][x]. */
+struct cr_net;
+
+/* Number of float32 parameters (weights W_l[co][ci][27] then biases b_l, layer by layer). */
+int64_t cr_net_param_count(void);
+
+/* New network for a D x H x W box and batches of up to batch_cap volumes;
+ * seeded initialisation with a zero last layer (the untrained network is Jacobi). */
+cr_status cr_net_create(int32_t D, int32_t H, int32_t W, int32_t batch_cap, uint64_t seed, void* stream,
+                        struct cr_net** out);
+void cr_net_destroy(struct cr_net* n);
+cr_status cr_net_get_params(struct cr_net* n, float* host, int64_t count);
+cr_status cr_net_set_params(struct cr_net* n, const float* host, int64_t count);
+
+/* out_dev (B x V) = net(in_dev (B x 2 x V)). */
+cr_status cr_net_forward(struct cr_net* n, int32_t B, const float* in_dev, float* out_dev);
+
+/* Loss = sum m (net(in) - target)^2 / sum m target^2 over the batch (mask_dev: V
+ * bytes) and its gradient with respect to every parameter (grad_host, may be NULL). */
+cr_status cr_net_gradients(struct cr_net* n, int32_t B, const float* in_dev, const float* target_dev,
+                           const uint8_t* mask_dev, float* loss_host, float* grad_host);
+
+/* One Adam step (beta1 0.9, beta2 0.999) on that loss; *loss_host (may be NULL) = loss before the step. */
+cr_status cr_net_train_step(struct cr_net* n, int32_t B, const float* in_dev, const float* target_dev,
+                            const uint8_t* mask_dev, float lr, float* loss_host);
+
+/* Voxel box of one side (0 = y grid of L_y, 1 = x grid of L_x): box_index_host[i]
+ * is the linear index z*H*W + y*W + x of row i; dims = {D, H, W}. */
+cr_status cr_set_voxel_grid(struct cr_problem* p, int32_t side, const int32_t* dims, const int32_t* box_index_host);
+
+/* Attach a network (NULL detaches); its box must match the voxel grids. */
+cr_status cr_set_preconditioner(struct cr_problem* p, struct cr_net* net);
+
 /* Static description of a status code. */
 const char* cr_status_str(cr_status s);
 

@@ -21,6 +21,7 @@ _lib = None
 
 CR_OK, CR_EINVAL, CR_ENOMEM, CR_ECUDA, CR_ENOTCONV, CR_ETIMEOUT, CR_ERANK, CR_ESTATE = range(8)
 CR_FP64, CR_MIXED = 0, 1
+CR_PRECOND_JACOBI, CR_PRECOND_LEARNED = 0, 1
 STOP_NAMES = {0: "none", 1: "r_max", 2: "dW", 3: "relres", 4: "rank"}
 
 _dp = C.POINTER(C.c_double)
@@ -93,6 +94,19 @@ SIGNATURES = {
     "cr_solve_v": (C.c_int, [C.c_void_p, _dp, _dp, _dp, _ip]),
     "cr_get_stats": (C.c_int, [C.c_void_p, C.POINTER(cr_stats), C.c_int32]),
     "cr_galerkin_assembly": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_float), C.c_int64]),
+    "cr_net_param_count": (C.c_int64, []),
+    "cr_net_create": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.c_void_p,
+                                C.POINTER(C.c_void_p)]),
+    "cr_net_destroy": (None, [C.c_void_p]),
+    "cr_net_get_params": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_int64]),
+    "cr_net_set_params": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_int64]),
+    "cr_net_forward": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "cr_net_gradients": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+    "cr_net_train_step": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_float,
+                                    C.POINTER(C.c_float)]),
+    "cr_set_voxel_grid": (C.c_int, [C.c_void_p, C.c_int32, _ip, _ip]),
+    "cr_set_preconditioner": (C.c_int, [C.c_void_p, C.c_void_p]),
     "cr_solve_u_noalloc": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_double,
                                      C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int32, _ip,
                                      C.c_void_p]),
@@ -311,6 +325,18 @@ class ConReg:
             G = buf.reshape(self.m, j, j).transpose(0, 2, 1).copy()
         return G
 
+    def cr_set_voxel_grid(self, side: int, mask: np.ndarray):
+        """Box of the active voxels of `mask` (C order), rows numbered in that order."""
+        dims = np.array(list(mask.shape) + [1] * (3 - mask.ndim), dtype=np.int32)
+        idx = np.ascontiguousarray(np.flatnonzero(mask.ravel()), dtype=np.int32)
+        _check(self._lib.cr_set_voxel_grid(self.h, int(side), _ptr(dims, _ip), _ptr(idx, _ip)), self.h,
+               "cr_set_voxel_grid")
+
+    def cr_set_preconditioner(self, net):
+        _check(self._lib.cr_set_preconditioner(self.h, net.h if net is not None else None), self.h,
+               "cr_set_preconditioner")
+        self._net = net
+
     def cr_get_stats(self, reset: bool = False) -> dict:
         s = cr_stats()
         _check(self._lib.cr_get_stats(self.h, C.byref(s), int(reset)), self.h, "cr_get_stats")
@@ -340,3 +366,74 @@ class ConReg:
 
 def cr_lambda_from_bar(lam_bar: float, ninj: int, nx: int) -> float:
     return load().cr_lambda_from_bar(float(lam_bar), int(ninj), int(nx))
+
+
+class ConvNet:
+    """The learned preconditioner's network (cr_net_*): 2 -> 16 -> 16 -> 16 -> 1
+    channels of 3x3x3 convolutions on a D x H x W box, trained on the GPU."""
+
+    def __init__(self, dims, batch_cap: int = 8, seed: int = 1808, stream=None):
+        import torch
+
+        self._lib = load()
+        d = list(dims) + [1] * (3 - len(dims))
+        self.dims = tuple(int(x) for x in d)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = C.c_void_p()
+        _check(self._lib.cr_net_create(self.dims[0], self.dims[1], self.dims[2], int(batch_cap), int(seed),
+                                       C.c_void_p(stream.cuda_stream), C.byref(h)), None, "cr_net_create")
+        self.h = h
+        self.V = self.dims[0] * self.dims[1] * self.dims[2]
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.cr_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def param_count() -> int:
+        return load().cr_net_param_count()
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.param_count(), dtype=np.float32)
+        _check(self._lib.cr_net_get_params(self.h, out.ctypes.data_as(C.POINTER(C.c_float)), out.size), None,
+               "cr_net_get_params")
+        return out
+
+    def set_params(self, w: np.ndarray):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        _check(self._lib.cr_net_set_params(self.h, w.ctypes.data_as(C.POINTER(C.c_float)), w.size), None,
+               "cr_net_set_params")
+
+    def forward(self, x):
+        """x: torch float32 (B, 2, D, H, W) on the GPU -> (B, D, H, W)."""
+        import torch
+
+        x = x.contiguous()
+        out = torch.empty((x.shape[0],) + self.dims, dtype=torch.float32, device=x.device)
+        _check(self._lib.cr_net_forward(self.h, x.shape[0], x.data_ptr(), out.data_ptr()), None, "cr_net_forward")
+        return out
+
+    def gradients(self, x, target, mask):
+        """Loss and parameter gradients (numpy, cr_net_param_count entries)."""
+        g = np.zeros(self.param_count(), dtype=np.float32)
+        loss = C.c_float()
+        _check(self._lib.cr_net_gradients(self.h, x.shape[0], x.contiguous().data_ptr(), target.contiguous().data_ptr(),
+                                          mask.contiguous().data_ptr(), C.byref(loss),
+                                          g.ctypes.data_as(C.POINTER(C.c_float))), None, "cr_net_gradients")
+        return loss.value, g
+
+    def train_step(self, x, target, mask, lr: float) -> float:
+        loss = C.c_float()
+        _check(self._lib.cr_net_train_step(self.h, x.shape[0], x.contiguous().data_ptr(), target.contiguous().data_ptr(),
+                                           mask.contiguous().data_ptr(), float(lr), C.byref(loss)), None,
+               "cr_net_train_step")
+        return loss.value

@@ -42,7 +42,7 @@ constexpr double kMixedPcgTol = 1e-6;
 
 enum {
   DS_UN2 = 0, DS_VN2 = 1, DS_NB = 2, DS_NA = 3, DS_DW = 4, /*5*/ DS_ZKZ = 6, DS_ZF = 7, DS_RN = 8, DS_V0 = 9,
-  DS_GS = 16, DS_COUNT = 32
+  DS_GS = 16, DS_FCG = 24, DS_COUNT = 32
 };
 
 struct HostScal {
@@ -87,6 +87,14 @@ struct cr_problem {
   int* gerr = nullptr;
   int gal_nb = 0;
   // float32 copies for the mixed form's inner Galerkin CG
+  // learned preconditioner: box index of each row per side, the network, its buffers
+  int* box[2] = {nullptr, nullptr};
+  int box_dims[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  cr_net* net = nullptr;
+  float *net_in = nullptr, *net_out = nullptr;
+  int64_t net_V = 0;
+  double *fc_rold = nullptr, *fc_d = nullptr, *fc_t = nullptr, *fc_y = nullptr;
+  int64_t fcg_fallbacks = 0;
   // BF16 hi/lo shadows of U (n_y x 128, column stride ldb) for the tensor-core assembly
   void *ubhi = nullptr, *ublo = nullptr;
   int64_t ldb = 0;
@@ -478,7 +486,74 @@ void prep_v(cr_problem* p, const double* uu) {
   omega_sq_dots(p->ny, p->m, p->Om, p->ny, uu, p->svec, st);
 }
 
+cr_status launch_pcg_jacobi(cr_problem* p, int side, const double* b, double* x, int maxit);
+
+// Flexible CG (Polak-Ribiere) with the learned preconditioner
+// z = D^-1 r + s net(D^-1 r / s, mask); float64 vectors.  If it has not
+// converged after pcg_maxit / 2 iterations the cluster Jacobi-PCG continues
+// from its iterate (fallback).  Writes the PcgStat of `side` like the PCG.
+cr_status fcg_learned(cr_problem* p, int side, const double* b, double* x) {
+  cudaStream_t st = p->st;
+  const DevLap& L = side == 0 ? p->Ly : p->Lx;
+  const int n = L.n;
+  const double* coef = p->coef + (side == 0 ? 0 : 2);
+  double* sc = p->ds + DS_FCG;
+  double *r = p->pr, *q = p->pw, *pv = p->pp, *z = p->ps, *rold = p->fc_rold, *dd = p->fc_d, *t = p->fc_t;
+  const double tol = p->opt.precision == CR_MIXED ? std::max(p->opt.pcg_tol, kMixedPcgTol) : p->opt.pcg_tol;
+  prof_begin(p, side == 0 ? CR_PHASE_PCG_U : CR_PHASE_PCG_V);
+  fcg_jacobi_diag(L, p->lam, coef, side, p->m, p->Om, p->ny, p->xi, p->xl, p->svec, p->pomt, p->pdinv, st);
+  fcg_apply(L, p->lam, coef, side, p->pomt, p->xl, p->xc_ptr, p->xc_row, p->xc_val, p->m, p->svec, p->fc_y, x, t, q,
+            st);
+  mat_axpby(n, 1, 1.0, b, n, -1.0, q, n, r, n, st);  // r = b - A x
+  dot(n, b, b, sc + 5, st);
+  fcg_precond(n, p->box[side], p->pdinv, r, sc + 4, p->net_in, p->net_V, p->net, p->net_out, z, st);
+  copy(n, z, pv, st);
+  dot(n, r, z, sc + 0, st);
+  dot(n, r, r, sc + 2, st);
+  TRY(readback(p, DS_FCG, 6, false));
+  const double bb = p->hs->ds[DS_FCG + 5];
+  const double tol2 = tol * tol * bb;
+  double rr = p->hs->ds[DS_FCG + 2];
+  const int cap = std::max(1, p->opt.pcg_maxit / 2);
+  int k = 0;
+  while (bb > 0.0 && rr > tol2 && k < cap) {
+    fcg_apply(L, p->lam, coef, side, p->pomt, p->xl, p->xc_ptr, p->xc_row, p->xc_val, p->m, p->svec, p->fc_y, pv, t,
+              q, st);
+    dot(n, pv, q, sc + 1, st);
+    fcg_update_xr(n, x, r, rold, pv, q, sc, st);
+    dot(n, r, r, sc + 2, st);
+    fcg_precond(n, p->box[side], p->pdinv, r, sc + 4, p->net_in, p->net_V, p->net, p->net_out, z, st);
+    fcg_diff(n, r, rold, dd, st);
+    dot(n, z, dd, sc + 3, st);
+    fcg_update_p(n, pv, z, sc, st);
+    dot(n, r, z, sc + 0, st);
+    ++k;
+    if (k < 8 || (k % 4) == 0) {
+      TRY(readback(p, DS_FCG, 3, false));
+      rr = p->hs->ds[DS_FCG + 2];
+      if (!std::isfinite(rr)) break;
+    }
+  }
+  prof_end(p, side == 0 ? CR_PHASE_PCG_U : CR_PHASE_PCG_V);
+  PcgStat hs{k, 0, bb > 0.0 ? std::sqrt(std::max(rr, 0.0) / bb) : 0.0, std::sqrt(bb)};
+  if (bb > 0.0 && !(rr <= tol2)) {
+    // fallback and judge: Jacobi-PCG from the current iterate
+    p->fcg_fallbacks += 1;
+    TRY(launch_pcg_jacobi(p, side, b, x, p->opt.pcg_maxit));
+    TRY(readback(p, 0, 1, true));
+    hs = p->hs->stat[side];
+    hs.iters += k;
+  }
+  CUCHK(p, cudaMemcpyAsync(p->stat + side, &hs, sizeof(PcgStat), cudaMemcpyHostToDevice, st));
+  return sync(p);
+}
+
 cr_status launch_pcg(cr_problem* p, int side, const double* b, double* x) {
+  if (p->opt.precond == CR_PRECOND_LEARNED && p->net && p->box[side]) return fcg_learned(p, side, b, x);
+  return launch_pcg_jacobi(p, side, b, x, p->opt.pcg_maxit);
+}
+
+cr_status launch_pcg_jacobi(cr_problem* p, int side, const double* b, double* x, int maxit) {
   PcgArgs a{};
   a.lam = p->lam;
   a.m = p->m;
@@ -494,7 +569,7 @@ cr_status launch_pcg(cr_problem* p, int side, const double* b, double* x) {
   // float32 vectors cannot resolve relative residuals much below 1e-6.
   a.fp32 = p->opt.precision == CR_MIXED;
   a.tol = a.fp32 ? std::max(p->opt.pcg_tol, kMixedPcgTol) : p->opt.pcg_tol;
-  a.maxit = p->opt.pcg_maxit;
+  a.maxit = maxit;
   a.stat = p->stat + side;
   a.force_generic = p->opt.pcg_kernel == 1;
   if (side == 0) {
@@ -1205,7 +1280,9 @@ cr_status cr_create(const cr_problem_desc* d, const cr_options* o, cr_problem** 
   const int nmax = (int)std::max(nx, ny);
   for (double** b : {&p->u, &p->uhat, &p->rhs_u, &p->tmpy}) CK(dalloc(p, b, ny));
   for (double** b : {&p->v, &p->vhat, &p->rhs_v, &p->tmpx}) CK(dalloc(p, b, nx));
-  for (double** b : {&p->pr, &p->pp, &p->ps, &p->pw, &p->pdinv, &p->pomt}) CK(dalloc(p, b, nmax));
+  for (double** b : {&p->pr, &p->pp, &p->ps, &p->pw, &p->pdinv, &p->pomt, &p->fc_rold, &p->fc_d, &p->fc_t})
+    CK(dalloc(p, b, nmax));
+  CK(dalloc(p, &p->fc_y, m));
   for (double** b : {&p->xi, &p->eta, &p->svec}) CK(dalloc(p, b, m));
   CK(dalloc(p, &p->hc, (size_t)3 * rc + m));
   CK(dalloc(p, &p->gc, (size_t)3 * rc + m));
@@ -1343,6 +1420,43 @@ cr_status cr_residual(cr_problem* p, double* relres, double* J, double* dW) {
   if (relres) TRY(do_relres(p, relres));
   prof_end(p, CR_PHASE_RESID);
   return CR_OK;
+}
+
+cr_status cr_set_voxel_grid(cr_problem* p, int32_t side, const int32_t* dims, const int32_t* box_index) {
+  if (!p || (side != 0 && side != 1) || !dims || !box_index) return CR_EINVAL;
+  const int n = side == 0 ? p->ny : p->nx;
+  const int64_t V = (int64_t)dims[0] * dims[1] * dims[2];
+  if (dims[0] < 1 || dims[1] < 1 || dims[2] < 1 || V > (1ll << 26)) return fail(p, CR_EINVAL, "bad box dimensions");
+  std::vector<int> idx(box_index, box_index + n);
+  std::vector<uint8_t> seen((size_t)V, 0);
+  for (int i = 0; i < n; ++i) {
+    if (idx[i] < 0 || idx[i] >= V || seen[idx[i]]) return fail(p, CR_EINVAL, "box indices out of range or repeated");
+    seen[idx[i]] = 1;
+  }
+  int* d = nullptr;
+  TRY(upload(p, &d, idx));
+  p->box[side] = d;
+  for (int k = 0; k < 3; ++k) p->box_dims[side][k] = dims[k];
+  return sync(p);
+}
+
+cr_status cr_set_preconditioner(cr_problem* p, cr_net* net) {
+  if (!p) return CR_EINVAL;
+  if (!net) {
+    p->net = nullptr;
+    return CR_OK;
+  }
+  const int64_t V = net_voxels(net);
+  for (int s = 0; s < 2; ++s)
+    if (p->box[s] && (int64_t)p->box_dims[s][0] * p->box_dims[s][1] * p->box_dims[s][2] != V)
+      return fail(p, CR_EINVAL, "network box does not match the voxel grid");
+  if (p->net_V != V) {
+    TRY(dalloc(p, &p->net_in, (size_t)2 * V));
+    TRY(dalloc(p, &p->net_out, (size_t)V));
+    p->net_V = V;
+  }
+  p->net = net;
+  return sync(p);
 }
 
 cr_status cr_galerkin_assembly(cr_problem* p, int32_t method, float* G_host, int64_t ldg) {

@@ -16,6 +16,8 @@
 
 #include <atomic>
 
+struct cr_net;
+
 namespace cr {
 
 // Number of kernels this library has launched (process-wide).
@@ -160,6 +162,22 @@ cudaError_t galerkin_cluster_f32_launch(int j, int m, int64_t ld, double lam, co
                                         const float* B1, const float* B2, const float* G, const float* H,
                                         const float* F, const float* Dg, float* Z, double tol2, int maxit,
                                         double* out, cudaStream_t st);
+
+// ---------------------------------------------------------------- cr_net.cu / cr_fcg.cu
+cudaError_t net_apply(cr_net* n, const float* in, float* out, cudaStream_t st);
+int64_t net_voxels(const cr_net* n);
+void fcg_jacobi_diag(const DevLap& L, double lam, const double* coef, int side, int m, const uint8_t* Om, int64_t ldo,
+                     const double* xi, const DevXLocal& X, const double* s, double* omt, double* dinv,
+                     cudaStream_t st);
+void fcg_apply(const DevLap& L, double lam, const double* coef, int side, const double* omt, const DevXLocal& X,
+               const int* xc_ptr, const int* xc_row, const double* xc_val, int m, const double* s, double* y,
+               const double* p, double* t, double* out, cudaStream_t st);
+void fcg_precond(int n, const int* box, const double* dinv, const double* r, double* s2, float* in, int64_t V,
+                 cr_net* net, float* out, double* z, cudaStream_t st);
+void fcg_update_xr(int n, double* x, double* r, double* rold, const double* p, const double* q, const double* sc,
+                   cudaStream_t st);
+void fcg_diff(int n, const double* r, const double* rold, double* d, cudaStream_t st);
+void fcg_update_p(int n, double* p, const double* z, const double* sc, cudaStream_t st);
 
 // ---------------------------------------------------------------- cr_tc.cu
 size_t tc_part_elems(int splits, int m);
