@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--learn-steps", type=int, default=200)
     return ap.parse_args()
 
 
@@ -222,16 +224,23 @@ def run_ours(args, rank, world, local_rank):
     p, cfg = workload(args, rank)
     stream = torch.cuda.current_stream()
     l2buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    from paper_1808_05510_gb300.conreg import CR_FP64, CR_MIXED
+    from paper_1808_05510_gb300.conreg import CR_FP64, CR_MIXED, CR_PRECOND_LEARNED
 
-    def measure(prec):
-        g = ConReg.from_problem(p, r_cap=args.r_max, profile=1, precision=prec)
+    def measure(prec, net=None, steps=None, warmup=None):
+        steps = args.steps if steps is None else steps
+        warmup = args.warmup if warmup is None else warmup
+        g = ConReg.from_problem(p, r_cap=args.r_max, profile=1, precision=prec,
+                                precond=CR_PRECOND_LEARNED if net is not None else 0)
+        if net is not None:
+            g.cr_set_voxel_grid(0, p.grid_y.mask)
+            g.cr_set_voxel_grid(1, p.grid_x.mask)
+            g.cr_set_preconditioner(net)
 
         def one_step():
             g.cr_set_factors(np.zeros((p.ny, 0)), np.zeros((0, 0)), np.zeros((p.nx, 0)))
             return g.cr_solve(args.r_max, args.tau, args.relres)
 
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             one_step()
             flush_l2(l2buf)
         torch.cuda.synchronize()
@@ -242,7 +251,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         ms, infos = [], []
         with ClockSampler(local_rank) as clk:
-            for _ in range(args.steps):
+            for _ in range(steps):
                 flush_l2(l2buf)
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
@@ -275,18 +284,37 @@ def run_ours(args, rank, world, local_rank):
         bytes_per_launch = iters_per_launch * pcg_bytes_per_iter(int(0.5 * (p.nx + p.ny)), word=word)
         avg_launch_s = pcg_ms / max(1, pcg_calls) / 1e3
         achieved = bytes_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
-        return {"value": value, "ms_per_step": t_max / args.steps, "time_to_relres_s": ttr,
+        return {"value": value, "ms_per_step": t_max / steps, "steps": steps, "time_to_relres_s": ttr,
                 "relres_reached_steps": len(reached), "final_relres": infos[-1]["relres"],
                 "final_rank": infos[-1]["rank"], "stop": infos[-1]["stop_name"],
-                "pcg_iters_per_step": stats["pcg_iters"] / args.steps,
-                "galerkin_cg_iters_per_step": sum(i["cg_iters"] for i in infos) / args.steps,
-                "phase_ms_per_step": {k: v / args.steps for k, v in stats["phase_ms"].items() if v},
+                "pcg_iters_per_step": stats["pcg_iters"] / steps,
+                "galerkin_cg_iters_per_step": sum(i["cg_iters"] for i in infos) / steps,
+                "phase_ms_per_step": {k: v / steps for k, v in stats["phase_ms"].items() if v},
                 "gpu_launches": stats["launches"], "clocks": clk.summary(),
                 "pcg": {"achieved": achieved, "avg_launch_us": avg_launch_s * 1e6, "iters_per_launch": iters_per_launch,
                         "us_per_iter": avg_launch_s * 1e6 / max(iters_per_launch, 1e-9),
-                        "share_of_step": pcg_ms / tot_ms if tot_ms > 0 else None}}
+                        "share_of_step": pcg_ms / tot_ms if tot_ms > 0 else None},
+                **({"judge": {"learned_solves": stats["learned_solves"], "fallbacks": stats["learned_fallbacks"],
+                              "switched_off_sides": [s for s in (0, 1) if stats["learned_off"] >> s & 1]}}
+                   if net is not None else {})}
 
     forms = {"fp64": measure(CR_FP64), "mixed": measure(CR_MIXED)}
+    if not args.no_learned:
+        # learned preconditioner: trained once (not timed) on the sub-systems of two
+        # other problems of the same family, then the float64 solve with flexible CG
+        from paper_1808_05510_gb300 import learned, synth as _synth
+
+        t0 = time.perf_counter()
+        train_probs = [_synth.visual_cortex(seed=1900 + k, lam=args.lam, r_max=args.r_max) for k in range(2)]
+        t1 = time.perf_counter()
+        net, hist, npairs = learned.train_for(train_probs, [0, 5, 10], steps=args.learn_steps, n_random=2, batch=8)
+        t2 = time.perf_counter()
+        lf = measure(CR_FP64, net=net, steps=1, warmup=0)
+        lf["training"] = {"pairs": npairs, "steps": args.learn_steps, "loss_first": float(np.mean(hist[:10])),
+                          "loss_last": float(np.mean(hist[-10:])), "seconds": t2 - t1,
+                          "problems": "2 visual-cortex-shaped problems, seeds 1900-1901, ranks 0/5/10, both sides"}
+        forms["learned"] = lf
+        net.close()
     head = forms[args.precision]
     hbm, peak_kind = peaks()
     roofline = {"bound": "hbm", "achieved": head["pcg"]["achieved"], "peak": hbm, "unit": "GB/s",

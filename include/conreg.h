@@ -148,6 +148,9 @@ typedef struct {
   int64_t h2d_bytes, d2h_bytes;   /* bytes this problem copied host->device / device->host */
   double phase_ms[CR_NPHASE];     /* device time per cr_phase (profile mode; else 0) */
   int64_t phase_calls[CR_NPHASE]; /* timed intervals per phase */
+  int64_t learned_solves;         /* sub-solves finished by the learned flexible CG */
+  int64_t learned_fallbacks;      /* learned solves that stagnated and were finished by Jacobi-PCG */
+  int64_t learned_off;            /* bit s set: the learned form is switched off for side s */
 } cr_stats;
 
 /* Fill *o with defaults (struct_size set).  Always succeeds for o != NULL. */
@@ -289,7 +292,13 @@ cr_status cr_net_train_step(struct cr_net* n, int32_t B, const float* in_dev, co
  * is the linear index z*H*W + y*W + x of row i; dims = {D, H, W}. */
 cr_status cr_set_voxel_grid(struct cr_problem* p, int32_t side, const int32_t* dims, const int32_t* box_index_host);
 
-/* Attach a network (NULL detaches); its box must match the voxel grids. */
+/* Attach a network (NULL detaches); its box must match the voxel grids.
+ * Jacobi-PCG judges the network, per side: the first sub-solve after attaching
+ * runs Jacobi-PCG and records its iteration count k_J; each later learned solve
+ * may take at most 2 k_J + 16 flexible-CG iterations, after which Jacobi-PCG
+ * finishes it from the current iterate (a fallback); three fallbacks in a row
+ * switch the learned form off for that side until the next attach.  cr_stats
+ * counts learned solves, fallbacks and the switched-off sides. */
 cr_status cr_set_preconditioner(struct cr_problem* p, struct cr_net* net);
 
 /* Static description of a status code. */

@@ -68,7 +68,8 @@ PHASES = ["pcg_u", "pcg_v", "rhs", "orth", "galerkin", "resid", "p6", "p7"]
 
 class cr_stats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("pcg_solves", C.c_int64), ("pcg_iters", C.c_int64),
-                ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("phase_ms", C.c_double * 8), ("phase_calls", C.c_int64 * 8)]
+                ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("phase_ms", C.c_double * 8), ("phase_calls", C.c_int64 * 8),
+                ("learned_solves", C.c_int64), ("learned_fallbacks", C.c_int64), ("learned_off", C.c_int64)]
 
 
 class cr_solve_info(C.Structure):
@@ -343,7 +344,9 @@ class ConReg:
         return {"launches": s.launches, "pcg_solves": s.pcg_solves, "pcg_iters": s.pcg_iters,
                 "h2d_bytes": s.h2d_bytes, "d2h_bytes": s.d2h_bytes,
                 "phase_ms": {PHASES[i]: s.phase_ms[i] for i in range(8)},
-                "phase_calls": {PHASES[i]: s.phase_calls[i] for i in range(8)}}
+                "phase_calls": {PHASES[i]: s.phase_calls[i] for i in range(8)},
+                "learned_solves": s.learned_solves, "learned_fallbacks": s.learned_fallbacks,
+                "learned_off": s.learned_off}
 
     def cr_solve_u(self, v, rhs):
         v = np.ascontiguousarray(v, dtype=np.float64)

@@ -94,7 +94,13 @@ struct cr_problem {
   float *net_in = nullptr, *net_out = nullptr;
   int64_t net_V = 0;
   double *fc_rold = nullptr, *fc_d = nullptr, *fc_t = nullptr, *fc_y = nullptr;
-  int64_t fcg_fallbacks = 0;
+  int64_t fcg_fallbacks = 0, learned_solves = 0;
+  // Jacobi as judge of the learned preconditioner, per side: the iteration count of
+  // a Jacobi-PCG solve (0 = not measured yet), consecutive fallbacks, and whether
+  // the learned form has been switched off for this side
+  int jac_iters[2] = {0, 0};
+  int learned_streak[2] = {0, 0};
+  bool learned_off[2] = {false, false};
   // BF16 hi/lo shadows of U (n_y x 128, column stride ldb) for the tensor-core assembly
   void *ubhi = nullptr, *ublo = nullptr;
   int64_t ldb = 0;
@@ -514,7 +520,9 @@ cr_status fcg_learned(cr_problem* p, int side, const double* b, double* x) {
   const double bb = p->hs->ds[DS_FCG + 5];
   const double tol2 = tol * tol * bb;
   double rr = p->hs->ds[DS_FCG + 2];
-  const int cap = std::max(1, p->opt.pcg_maxit / 2);
+  // stagnation check: the flexible CG may take at most twice the judge's
+  // Jacobi-PCG iterations (plus a margin) before it gives up
+  const int cap = std::max(1, std::min(p->opt.pcg_maxit / 2, 2 * p->jac_iters[side] + 16));
   int k = 0;
   while (bb > 0.0 && rr > tol2 && k < cap) {
     fcg_apply(L, p->lam, coef, side, p->pomt, p->xl, p->xc_ptr, p->xc_row, p->xc_val, p->m, p->svec, p->fc_y, pv, t,
@@ -537,19 +545,31 @@ cr_status fcg_learned(cr_problem* p, int side, const double* b, double* x) {
   prof_end(p, side == 0 ? CR_PHASE_PCG_U : CR_PHASE_PCG_V);
   PcgStat hs{k, 0, bb > 0.0 ? std::sqrt(std::max(rr, 0.0) / bb) : 0.0, std::sqrt(bb)};
   if (bb > 0.0 && !(rr <= tol2)) {
-    // fallback and judge: Jacobi-PCG from the current iterate
+    // fallback: Jacobi-PCG from the current iterate; three fallbacks in a row
+    // switch the learned form off for this side
     p->fcg_fallbacks += 1;
+    if (++p->learned_streak[side] >= 3) p->learned_off[side] = true;
     TRY(launch_pcg_jacobi(p, side, b, x, p->opt.pcg_maxit));
     TRY(readback(p, 0, 1, true));
     hs = p->hs->stat[side];
     hs.iters += k;
+  } else {
+    p->learned_streak[side] = 0;
+    p->learned_solves += 1;
   }
   CUCHK(p, cudaMemcpyAsync(p->stat + side, &hs, sizeof(PcgStat), cudaMemcpyHostToDevice, st));
   return sync(p);
 }
 
 cr_status launch_pcg(cr_problem* p, int side, const double* b, double* x) {
-  if (p->opt.precond == CR_PRECOND_LEARNED && p->net && p->box[side]) return fcg_learned(p, side, b, x);
+  if (p->opt.precond == CR_PRECOND_LEARNED && p->net && p->box[side] && !p->learned_off[side]) {
+    if (p->jac_iters[side] > 0) return fcg_learned(p, side, b, x);
+    // first solve on this side: Jacobi-PCG, whose iteration count judges the learned form
+    TRY(launch_pcg_jacobi(p, side, b, x, p->opt.pcg_maxit));
+    TRY(readback(p, 0, 1, true));
+    p->jac_iters[side] = std::max(1, p->hs->stat[side].iters);
+    return CR_OK;
+  }
   return launch_pcg_jacobi(p, side, b, x, p->opt.pcg_maxit);
 }
 
@@ -1456,6 +1476,10 @@ cr_status cr_set_preconditioner(cr_problem* p, cr_net* net) {
     p->net_V = V;
   }
   p->net = net;
+  for (int s = 0; s < 2; ++s) {
+    p->jac_iters[s] = p->learned_streak[s] = 0;
+    p->learned_off[s] = false;
+  }
   return sync(p);
 }
 
@@ -1490,6 +1514,9 @@ cr_status cr_get_stats(cr_problem* p, cr_stats* s, int32_t reset) {
   s->pcg_iters = p->pcg_iters;
   s->h2d_bytes = p->h2d_bytes;
   s->d2h_bytes = p->d2h_bytes;
+  s->learned_solves = p->learned_solves;
+  s->learned_fallbacks = p->fcg_fallbacks;
+  s->learned_off = (p->learned_off[0] ? 1 : 0) | (p->learned_off[1] ? 2 : 0);
   for (int i = 0; i < CR_NPHASE; ++i) {
     s->phase_ms[i] = p->phase_ms[i];
     s->phase_calls[i] = p->phase_calls[i];
@@ -1498,6 +1525,7 @@ cr_status cr_get_stats(cr_problem* p, cr_stats* s, int32_t reset) {
     p->launch_base = cr::g_launches.load();
     p->pcg_solves = p->pcg_iters = 0;
     p->h2d_bytes = p->d2h_bytes = 0;
+    p->learned_solves = p->fcg_fallbacks = 0;
     for (int i = 0; i < CR_NPHASE; ++i) {
       p->phase_ms[i] = 0.0;
       p->phase_calls[i] = 0;

@@ -36,7 +36,6 @@ def box_mask(grid) -> np.ndarray:
 
 def jacobi_diag(p: Problem, v: np.ndarray) -> np.ndarray:
     """Diagonal of A_hat (Eq. ALS_linsys) for unit v: lam((L_y^2)_ii + 2c (L_y)_ii + d) + omega_i."""
-    Ly = p.Ly.to_dense() if p.ny <= 2000 else None
     Lx_v = _csr_mul(p.Lx, v)
     c = float(v @ Lx_v)
     d = float(Lx_v @ Lx_v)
@@ -50,8 +49,24 @@ def jacobi_diag(p: Problem, v: np.ndarray) -> np.ndarray:
                 diag[i] += val
     xi = p.X.T @ v
     omega = p.Omega.astype(np.float64) @ (xi * xi)
-    del Ly
     return p.lam * (l2 + 2.0 * c * diag + d) + omega
+
+
+def jacobi_diag_v(p: Problem, u: np.ndarray) -> np.ndarray:
+    """Diagonal of B_hat (Eq. ALS_linsys_v) for unit u: lam((L_x^2)_kk + 2c' (L_x)_kk + d') + sum_a s_a X_ka^2."""
+    Ly_u = _csr_mul(p.Ly, u)
+    c = float(u @ Ly_u)
+    d = float(Ly_u @ Ly_u)
+    diag = np.zeros(p.nx)
+    l2 = np.zeros(p.nx)
+    for i in range(p.nx):
+        for q in range(p.Lx.rowptr[i], p.Lx.rowptr[i + 1]):
+            val = p.Lx.val[q]
+            l2[i] += val * val
+            if p.Lx.col[q] == i:
+                diag[i] += val
+    s = p.Omega.astype(np.float64).T @ (u * u)
+    return p.lam * (l2 + 2.0 * c * diag + d) + (p.X * p.X) @ s
 
 
 def _csr_mul(L, x):
@@ -70,9 +85,10 @@ def _to_box(mask3: np.ndarray, vec: np.ndarray) -> np.ndarray:
     return out
 
 
-def smooth_field(p: Problem, rng: np.random.Generator, bumps: int = 6) -> np.ndarray:
-    c = p.grid_y.unit_coords()
-    f = np.zeros(p.ny)
+def smooth_field(p: Problem, rng: np.random.Generator, bumps: int = 6, side: int = 0) -> np.ndarray:
+    """Sum of random Gaussian bumps on the y grid (side 0) or the x grid (side 1)."""
+    c = (p.grid_y if side == 0 else p.grid_x).unit_coords()
+    f = np.zeros(len(c))
     for _ in range(bumps):
         ctr = c[rng.integers(len(c))]
         w = rng.uniform(0.05, 0.3)
@@ -80,11 +96,25 @@ def smooth_field(p: Problem, rng: np.random.Generator, bumps: int = 6) -> np.nda
     return f
 
 
-def make_pairs(p: Problem, ranks: List[int], n_random: int = 4, seed: int = 0, tol: float = 1e-9) -> List[Pair]:
-    """(input, target) pairs from the u-side systems the greedy solver meets at the given ranks."""
+def make_pairs(p: Problem, ranks: List[int], n_random: int = 4, seed: int = 0, tol: float = 1e-9,
+               sides=(0, 1)) -> List[Pair]:
+    """(input, target) pairs from the sub-systems the greedy solver meets at the
+    given ranks: u side (Eq. ALS_linsys) for the ALS start vector v, v side
+    (Eq. ALS_linsys_v) for u = u_hat / |u_hat|, each with its right side from the
+    residual plus n_random smooth random right sides."""
     rng = np.random.default_rng(seed)
-    mask3 = box_mask(p.grid_y)
+    masks = [box_mask(p.grid_y), box_mask(p.grid_x)]
     pairs: List[Pair] = []
+
+    def add(side, r, e, Dg):
+        jr = r / Dg
+        s = float(np.linalg.norm(jr))
+        if s == 0.0:
+            return
+        m3 = masks[side]
+        x = np.stack([_to_box(m3, jr / s), m3.astype(np.float32)])
+        pairs.append(Pair(x.astype(np.float32), _to_box(m3, (e - jr) / s)))
+
     with conreg.ConReg.from_problem(p, r_cap=max(max(ranks), 1), pcg_tol=tol, pcg_maxit=100000) as g:
         done = 0
         for j in sorted(ranks):
@@ -93,16 +123,22 @@ def make_pairs(p: Problem, ranks: List[int], n_random: int = 4, seed: int = 0, t
                 done = g.cr_get_rank()
             v = g.cr_apply_residual(np.ones(p.ny), trans=True)
             v /= np.linalg.norm(v)
-            Dg = jacobi_diag(p, v)
-            rhss = [g.cr_apply_residual(v)] + [smooth_field(p, rng) for _ in range(n_random)]
-            for r in rhss:
-                e, _ = g.cr_solve_u(v, r)
-                jr = r / Dg
-                s = float(np.linalg.norm(jr))
-                if s == 0.0:
-                    continue
-                x = np.stack([_to_box(mask3, jr / s), mask3.astype(np.float32)])
-                pairs.append(Pair(x.transpose(0, 1, 2, 3).astype(np.float32), _to_box(mask3, (e - jr) / s)))
+            Du = jacobi_diag(p, v)
+            ru = g.cr_apply_residual(v)
+            eu, _ = g.cr_solve_u(v, ru)
+            if 0 in sides:
+                add(0, ru, eu, Du)
+                for _ in range(n_random):
+                    r = smooth_field(p, rng)
+                    add(0, r, g.cr_solve_u(v, r)[0], Du)
+            if 1 in sides:
+                u = eu / np.linalg.norm(eu)
+                Dv = jacobi_diag_v(p, u)
+                rv = g.cr_apply_residual(u, trans=True)
+                add(1, rv, g.cr_solve_v(u, rv)[0], Dv)
+                for _ in range(n_random):
+                    r = smooth_field(p, rng, side=1)
+                    add(1, r, g.cr_solve_v(u, r)[0], Dv)
     return pairs
 
 
@@ -126,8 +162,12 @@ def train(net: "conreg.ConvNet", pairs: List[Pair], steps: int = 300, lr: float 
     return hist
 
 
-def compare_iterations(p: Problem, net: "conreg.ConvNet", ranks: List[int], tol: float = 1e-8):
-    """Iterations of Jacobi-PCG and of the learned flexible CG on the same u-side systems."""
+def compare_iterations(p: Problem, net: "conreg.ConvNet", ranks: List[int], tol: float = 1e-8, sides=(0,)):
+    """Iterations of Jacobi-PCG and of the learned flexible CG on the same sub-systems.
+
+    The learned problem's first solve on each side is its Jacobi judge run
+    (cr_set_preconditioner), so one calibration solve per side precedes the
+    measured ones."""
     out = []
     with conreg.ConReg.from_problem(p, r_cap=max(max(ranks), 1), pcg_tol=tol, pcg_maxit=100000) as gj, \
             conreg.ConReg.from_problem(p, r_cap=max(max(ranks), 1), pcg_tol=tol, pcg_maxit=100000,
@@ -136,6 +176,7 @@ def compare_iterations(p: Problem, net: "conreg.ConvNet", ranks: List[int], tol:
         gl.cr_set_voxel_grid(1, p.grid_x.mask)
         gl.cr_set_preconditioner(net)
         done = 0
+        calibrated = False
         for j in sorted(ranks):
             if j > done:
                 gj.cr_solve(j, 0.0, 0.0)
@@ -147,7 +188,31 @@ def compare_iterations(p: Problem, net: "conreg.ConvNet", ranks: List[int], tol:
             v /= np.linalg.norm(v)
             r = gj.cr_apply_residual(v)
             ej, itj = gj.cr_solve_u(v, r)
-            el, itl = gl.cr_solve_u(v, r)
-            out.append({"rank": j, "iters_jacobi": itj, "iters_learned": itl,
-                        "rel_diff": float(np.linalg.norm(el - ej) / np.linalg.norm(ej))})
+            if not calibrated:
+                gl.cr_solve_u(v, r)
+                gl.cr_solve_v(ej / np.linalg.norm(ej), gj.cr_apply_residual(ej / np.linalg.norm(ej), trans=True))
+                calibrated = True
+            if 0 in sides:
+                el, itl = gl.cr_solve_u(v, r)
+                out.append({"rank": j, "side": "u", "iters_jacobi": itj, "iters_learned": itl,
+                            "rel_diff": float(np.linalg.norm(el - ej) / np.linalg.norm(ej))})
+            if 1 in sides:
+                u = ej / np.linalg.norm(ej)
+                rv = gj.cr_apply_residual(u, trans=True)
+                fj, itj2 = gj.cr_solve_v(u, rv)
+                fl, itl2 = gl.cr_solve_v(u, rv)
+                out.append({"rank": j, "side": "v", "iters_jacobi": itj2, "iters_learned": itl2,
+                            "rel_diff": float(np.linalg.norm(fl - fj) / np.linalg.norm(fj))})
     return out
+
+
+def train_for(problems: List[Problem], ranks: List[int], steps: int = 300, n_random: int = 3, batch: int = 8,
+              lr: float = 2e-3, seed: int = 1):
+    """Pairs from every problem (both sides) and a trained network on their common box."""
+    pairs = []
+    for k, p in enumerate(problems):
+        pairs += make_pairs(p, ranks, n_random=n_random, seed=seed + k)
+    shape = pairs[0].t.shape
+    net = conreg.ConvNet(shape, batch_cap=batch, seed=seed)
+    hist = train(net, pairs, steps=steps, lr=lr, batch=batch, seed=seed)
+    return net, hist, len(pairs)

@@ -125,17 +125,19 @@ def grid_laplacian(grid: Grid) -> CSR:
             nbrs.append(j)
     nbrs = np.stack(nbrs, axis=1)  # (n, 2d)
     deg = (nbrs >= 0).sum(axis=1)
-    rows, cols, vals = [], [], []
-    for i in range(n):
-        entries = [(i, float(deg[i]))] + [(int(j), -1.0) for j in nbrs[i] if j >= 0]
-        entries.sort()
-        for j, v in entries:
-            rows.append(i)
-            cols.append(j)
-            vals.append(v)
-    rowptr = np.zeros(n + 1, dtype=np.int32)
-    np.add.at(rowptr, np.asarray(rows) + 1, 1)
+    # entries (i, i, deg_i) and (i, j, -1) for every face neighbour j, sorted by (row, column)
+    ri = np.repeat(np.arange(n), nbrs.shape[1])
+    cj = nbrs.ravel()
+    keep = cj >= 0
+    rows = np.concatenate([np.arange(n), ri[keep]])
+    cols_ = np.concatenate([np.arange(n), cj[keep]])
+    vals = np.concatenate([deg.astype(np.float64), -np.ones(int(keep.sum()))])
+    order = np.lexsort((cols_, rows))
+    rows, cols_, vals = rows[order], cols_[order], vals[order]
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rowptr, rows + 1, 1)
     rowptr = np.cumsum(rowptr).astype(np.int32)
+    cols = cols_
     return CSR(n, rowptr, np.asarray(cols, dtype=np.int32), np.asarray(vals, dtype=np.float64))
 
 
@@ -225,7 +227,8 @@ def w_true_block(py: np.ndarray, px: np.ndarray, sparse_cut: float = 0.0) -> np.
     d = py.shape[1]
     a = 0.8 * np.ones(d)
     b = 0.1 * np.ones(d)
-    d2 = ((py[:, None, :] - px[None, :, :]) ** 2).sum(-1)
+    d2 = (py * py).sum(1)[:, None] + (px * px).sum(1)[None, :] - 2.0 * (py @ px.T)
+    np.maximum(d2, 0.0, out=d2)
     w = np.exp(-d2 / 0.16)
     w += 0.9 * np.exp(-(((px - a) ** 2).sum(-1)[None, :] + ((py - b) ** 2).sum(-1)[:, None]) / 0.04)
     if sparse_cut > 0.0:

@@ -77,7 +77,8 @@ def test_network_forward_and_gradients_match_oracle(env):
 
 def test_untrained_network_is_jacobi(env):
     """The last layer starts at zero, so the flexible CG with the untrained net
-    takes the same iterations as Jacobi-PCG and gives the same solution."""
+    is Jacobi-PCG with the Polak-Ribiere beta: the same solution, and the same
+    iterations up to rounding (the two betas agree only in exact arithmetic)."""
     torch, cr = env
     from paper_1808_05510_gb300 import learned
 
@@ -86,7 +87,7 @@ def test_untrained_network_is_jacobi(env):
     res = learned.compare_iterations(p, net, [2])
     for r in res:
         assert r["rel_diff"] < 1e-6
-        assert abs(r["iters_learned"] - r["iters_jacobi"]) <= 2
+        assert abs(r["iters_learned"] - r["iters_jacobi"]) <= max(2, 0.05 * r["iters_jacobi"])
     net.close()
 
 
@@ -99,7 +100,7 @@ def test_learned_preconditioner_gain(env):
     train = [synth.toy2d(seed=s) for s in (11, 12, 13)]
     pairs = []
     for k, p in enumerate(train):
-        pairs += learned.make_pairs(p, [0, 2, 4, 6, 8], n_random=6, seed=k)
+        pairs += learned.make_pairs(p, [0, 2, 4, 6, 8], n_random=6, seed=k, sides=(0,))
     net = cr.ConvNet(learned.box_mask(train[0].grid_y).shape, batch_cap=8, seed=1)
     hist = learned.train(net, pairs, steps=400, lr=2e-3, batch=8)
     assert np.mean(hist[-20:]) < 0.8 * np.mean(hist[:20])
@@ -109,4 +110,57 @@ def test_learned_preconditioner_gain(env):
     for r in res:
         assert r["rel_diff"] < 1e-6
     assert sum(r["iters_learned"] for r in res) < sum(r["iters_jacobi"] for r in res)
+    net.close()
+
+
+def test_learned_preconditioner_both_sides_blob_mask(env):
+    """Trained on both sides of 3-D blob-mask problems: the flexible CG reaches
+    the Jacobi-PCG solution on held-out u- and v-side systems."""
+    torch, cr = env
+    from paper_1808_05510_gb300 import learned
+
+    train = [synth.masked3d(seed=s) for s in (21, 22)]
+    # the same box for every problem of the family
+    net, hist, npairs = learned.train_for(train, [0, 3, 6], steps=200, n_random=2, batch=8)
+    assert npairs > 20 and np.mean(hist[-20:]) < np.mean(hist[:20])
+    test = synth.masked3d(seed=29)
+    res = learned.compare_iterations(test, net, [0, 4], sides=(0, 1))
+    print(res)
+    for r in res:
+        assert r["rel_diff"] < 1e-6
+    net.close()
+
+
+def test_garbage_network_falls_back_to_jacobi(env):
+    """A network with large random weights: every learned solve stagnates, is
+    finished by Jacobi-PCG (same solution), and after three fallbacks in a row
+    the learned form is switched off for that side."""
+    torch, cr = env
+    from paper_1808_05510_gb300 import learned
+
+    p = synth.toy2d()
+    net = cr.ConvNet(learned.box_mask(p.grid_y).shape, batch_cap=1)
+    rng = np.random.default_rng(5)
+    net.set_params((5.0 * rng.standard_normal(net.param_count())).astype(np.float32))
+    with cr.ConReg.from_problem(p, r_cap=4, pcg_tol=1e-9, pcg_maxit=100000) as gj, \
+            cr.ConReg.from_problem(p, r_cap=4, pcg_tol=1e-9, pcg_maxit=100000,
+                                   precond=cr.CR_PRECOND_LEARNED) as gl:
+        gl.cr_set_voxel_grid(0, p.grid_y.mask)
+        gl.cr_set_voxel_grid(1, p.grid_x.mask)
+        gl.cr_set_preconditioner(net)
+        gl.cr_get_stats(reset=True)
+        v = gj.cr_apply_residual(np.ones(p.ny), trans=True)
+        v /= np.linalg.norm(v)
+        r = gj.cr_apply_residual(v)
+        ej, itj = gj.cr_solve_u(v, r)
+        its = []
+        for _ in range(5):
+            el, itl = gl.cr_solve_u(v, r)
+            its.append(itl)
+            assert np.linalg.norm(el - ej) <= 1e-6 * np.linalg.norm(ej)
+        st = gl.cr_get_stats()
+        assert its[0] == itj  # the judge run is Jacobi-PCG
+        assert st["learned_fallbacks"] == 3 and st["learned_solves"] == 0
+        assert st["learned_off"] & 1
+        assert its[4] == itj  # switched off: plain Jacobi-PCG again
     net.close()
