@@ -16,7 +16,8 @@ the number of library kernel launches.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 For N > 1 (torchrun, one process per GPU) every rank solves its own replica
-of the workload (a single greedy solve does not shard) and rank 0
+of the workload (a single greedy solve is a chain of dependent steps with a
+global reduction in every PCG iteration, so it does not shard) and rank 0
 reports the aggregate over ranks divided by the slowest rank's time.
 """
 from __future__ import annotations

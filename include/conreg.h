@@ -102,6 +102,8 @@ typedef struct {
   void* (*alloc)(size_t bytes, void* ctx);
   void (*free)(void* ptr, size_t bytes, void* ctx);
   void* alloc_ctx;
+  int32_t galerkin_ctas;   /* CTA cap of the persistent Galerkin kernel; 0 = one CTA per SM.  Problems
+                              that share the GPU (cr_solve_batch) cap it so that their launches co-run. */
 } cr_options;
 
 typedef struct {
@@ -253,6 +255,60 @@ cr_status cr_get_stats(struct cr_problem* p, cr_stats* s, int32_t reset);
 cr_status cr_solve_u_noalloc(int64_t n, const int32_t* rowptr_dev, const int32_t* col_dev, const double* val_dev,
                              double lambda, double c, double d, const double* omega_dev, const double* rhs_dev,
                              double* u_hat_dev, double tol, int32_t maxit, int32_t* iters, void* stream);
+
+/* Held-out (cross-validation) error of the current W = U Z V^T on mt
+ * injections that the fit did not use: X_t (nx x mt, ld ldx), Y_t (ny x mt,
+ * ld ldy), Omega_t (ny x mt, ld ldo), all host memory.  On return
+ *   *num = sum_a |(W x_a - y_a) o omega_a|^2,   *den = sum_a |y_a o omega_a|^2,
+ * the data term of Eq. (obj_fun) (times 2) evaluated on the held-out columns,
+ * and its value at W = 0.  The products run on the device as V^T X_t, then
+ * Z (V^T X_t), then U Z V^T X_t; the two sums are deterministic reductions.
+ * The paper fixes lambda-bar by hand (Sec. 1.1); scoring held-out injections
+ * is this library's criterion for the lambda x fold sweep below. */
+cr_status cr_cv_error(struct cr_problem* p, int32_t mt, const double* Xt_host, int64_t ldx, const double* Yt_host,
+                      int64_t ldy, const uint8_t* Omega_t_host, int64_t ldo, double* num, double* den);
+
+/* ---- batched lambda x fold sweep -------------------------------------------
+ * Independent greedy solves (Algorithm 1) of sub-problems of one data set: a
+ * member fits the injections fit_cols (columns of X, Y, Omega) with its own
+ * lambda, and is scored on test_cols by cr_cv_error.  Members differ in lambda
+ * and in their (uneven) injection counts. */
+typedef struct {
+  double lambda;             /* weight of Eq. (obj_fun) for this member */
+  const int32_t* fit_cols;   /* host: injections the member fits (n_fit >= 1, each in [0, ninj)) */
+  int32_t n_fit;
+  const int32_t* test_cols;  /* host: held-out injections scored after the solve (may be NULL) */
+  int32_t n_test;
+} cr_member;
+
+typedef struct {
+  int32_t status;            /* cr_status of the member (CR_ENOTCONV: stopped early, results valid) */
+  int32_t rank;              /* final rank */
+  int32_t stop;              /* cr_stop */
+  int32_t slot;              /* worker slot that ran the member */
+  double relres, dW, J;      /* as in cr_solve_info */
+  double cv_num, cv_den;     /* cr_cv_error on test_cols (0, 0 without test columns) */
+  int64_t pcg_iters, cg_iters;
+  double seconds;            /* host wall time of the member's solve and scoring */
+} cr_member_result;
+
+/* Solve every member: `concurrency` worker threads (0 = one per 16 SMs), each
+ * with its own CUDA stream, take members longest first (largest lambda first)
+ * and run create -> cr_solve(r_max, tau, relres_target) -> cr_cv_error on them,
+ * so that as many greedy solves as the GPU holds run at once (each PCG solve
+ * occupies one thread-block cluster).  desc holds the full data set (its
+ * lambda is ignored); opts apply to every member (opts->stream, when set, is
+ * the stream that the workers' streams fork from and join into, so CUDA events
+ * recorded on it around the call time the whole sweep).  Each member's device
+ * memory stays allocated until the sweep ends (no device-synchronising frees
+ * while members run).  keep (may be NULL) receives the n_members problem
+ * handles, which the caller then owns (cr_destroy); otherwise they are
+ * destroyed before return.  results[k] describes members[k].  Returns CR_OK
+ * when every member's status is CR_OK or CR_ENOTCONV, else the first other
+ * status (all results are filled either way); CR_EINVAL for bad arguments. */
+cr_status cr_solve_batch(const cr_problem_desc* desc, const cr_options* opts, const cr_member* members,
+                         int32_t n_members, int32_t r_max, double tau, double relres_target, int32_t concurrency,
+                         cr_member_result* results, struct cr_problem** keep);
 
 /* ---- learned preconditioner (the paper has no counterpart: its sub-problems
  * are solved directly) ------------------------------------------------------

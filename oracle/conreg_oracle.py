@@ -16,7 +16,7 @@ slow restatement of the paper (Kuerschner, Dolgov, Harris, Benner,
 
 Library primitives (dense/sparse matrix products, Cholesky) serve as single
 steps; nothing is blocked or fused beyond what the equations state.  Where the
-paper is silent the oracle takes these readings (listed again in the design doc):
+paper is silent the oracle takes these readings:
 
 * ALS start vector: ``v0 = R_j^T 1 / ||R_j^T 1||`` (a seeded Gaussian if that
   norm vanishes); at least one ALS sweep, at most ``als_max_iter``; the sweep
@@ -320,6 +320,20 @@ class Oracle:
         Z, it, _ = cg(lambda Zm: self.K_apply(Zm, A1, A2, B1, B2, G, Hs), F, x0=Z0, tol=tol,
                       maxit=maxit or 10 * j * j + 100, inner=lambda a, c: float(np.sum(a * c)))
         return Z, it
+
+    # --- held-out scoring -------------------------------------------------------
+    @staticmethod
+    def cv_error(U, Z, V, Xt, Yt, Omt):
+        """Twice the data term of Eq. (obj_fun) on held-out injections, for
+        W = U Z V^T: (sum |(W X_t - Y_t) o Omega_t|^2, sum |Y_t o Omega_t|^2).
+        The second value is the first at W = 0.  (The paper fixes lambda-bar
+        by hand, Sec. 1.1; scoring held-out injections is the reading used for
+        the lambda x fold sweep.)"""
+        Om = np.asarray(Omt, dtype=np.float64)
+        W = np.asarray(U) @ np.asarray(Z) @ np.asarray(V).T
+        E = (W @ np.asarray(Xt) - np.asarray(Yt)) * Om
+        Y0 = np.asarray(Yt) * Om
+        return float(np.sum(E * E)), float(np.sum(Y0 * Y0))
 
     # --- Algorithm 1 -------------------------------------------------------------
     def greedy(self, r_max: int, tau: float = 1e-12, relres_target: float = 0.0, als_delta: float = 0.1,

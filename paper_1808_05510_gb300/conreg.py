@@ -50,7 +50,7 @@ class cr_options(C.Structure):
                 ("galerkin_maxit", C.c_int32), ("residual_every", C.c_int32), ("cluster_size", C.c_int32),
                 ("profile", C.c_int32), ("pcg_kernel", C.c_int32), ("galerkin_kernel", C.c_int32),
                 ("seed", C.c_uint64), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
-                ("alloc_ctx", C.c_void_p)]
+                ("alloc_ctx", C.c_void_p), ("galerkin_ctas", C.c_int32)]
 
 
 class cr_rank1_info(C.Structure):
@@ -75,6 +75,17 @@ class cr_stats(C.Structure):
 class cr_solve_info(C.Structure):
     _fields_ = [("rank", C.c_int32), ("stop", C.c_int32), ("relres", C.c_double), ("dW", C.c_double),
                 ("J", C.c_double), ("pcg_iters", C.c_int64), ("cg_iters", C.c_int64), ("seconds", C.c_double)]
+
+
+class cr_member(C.Structure):
+    _fields_ = [("lambda_", C.c_double), ("fit_cols", _ip), ("n_fit", C.c_int32), ("test_cols", _ip),
+                ("n_test", C.c_int32)]
+
+
+class cr_member_result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("rank", C.c_int32), ("stop", C.c_int32), ("slot", C.c_int32),
+                ("relres", C.c_double), ("dW", C.c_double), ("J", C.c_double), ("cv_num", C.c_double),
+                ("cv_den", C.c_double), ("pcg_iters", C.c_int64), ("cg_iters", C.c_int64), ("seconds", C.c_double)]
 
 
 # Every exported symbol with its (restype, argtypes); include/conreg.h declares the same set.
@@ -111,6 +122,10 @@ SIGNATURES = {
     "cr_solve_u_noalloc": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_double,
                                      C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int32, _ip,
                                      C.c_void_p]),
+    "cr_cv_error": (C.c_int, [C.c_void_p, C.c_int32, _dp, C.c_int64, _dp, C.c_int64, _up, C.c_int64, _dp, _dp]),
+    "cr_solve_batch": (C.c_int, [C.POINTER(cr_problem_desc), C.POINTER(cr_options), C.POINTER(cr_member), C.c_int32,
+                                 C.c_int32, C.c_double, C.c_double, C.c_int32, C.POINTER(cr_member_result),
+                                 C.POINTER(C.c_void_p)]),
     "cr_status_str": (C.c_char_p, [C.c_int]),
     "cr_last_error": (C.c_char_p, [C.c_void_p]),
 }
@@ -302,6 +317,28 @@ class ConReg:
                    "cr_get_factors")
         return U, Z, V
 
+    def cr_cv_error(self, Xt, Yt, Omt):
+        """(sum_a |(W x_a - y_a) o omega_a|^2, sum_a |y_a o omega_a|^2) over held-out columns."""
+        Xt, Yt = _f64(Xt), _f64(Yt)
+        Omt = np.asfortranarray(np.asarray(Omt, dtype=np.uint8))
+        mt = Xt.shape[1]
+        num, den = C.c_double(), C.c_double()
+        _check(self._lib.cr_cv_error(self.h, mt, _ptr(Xt), max(1, self.nx), _ptr(Yt), max(1, self.ny),
+                                     _ptr(Omt, _up), max(1, self.ny), C.byref(num), C.byref(den)), self.h,
+               "cr_cv_error")
+        return num.value, den.value
+
+    @classmethod
+    def _adopt(cls, handle, nx: int, ny: int, lam: float) -> "ConReg":
+        """Wrap a problem handle that the library created (cr_solve_batch's kept members)."""
+        g = cls.__new__(cls)
+        g._lib = load()
+        g._keep = []
+        g._allocator = None
+        g.nx, g.ny, g.lam = nx, ny, float(lam)
+        g.h = C.c_void_p(handle)
+        return g
+
     def cr_set_factors(self, U, Z, V):
         U, Z, V = _f64(U), _f64(Z), _f64(V)
         j = Z.shape[0]
@@ -365,6 +402,69 @@ class ConReg:
         st = self._lib.cr_solve_v(self.h, _ptr(u), _ptr(rhs), _ptr(out), C.byref(it))
         _check(st, self.h, "cr_solve_v")
         return out, it.value
+
+
+def solve_batch(p, members, r_max: int, tau: float = 0.0, relres_target: float = 0.0, concurrency: int = 0,
+                keep: bool = False, stream=None, **opts):
+    """cr_solve_batch on the data set of problem ``p`` (Lx, Ly, X, Y, Omega).
+
+    ``members``: list of (lambda, fit_cols, test_cols).  Returns one dict per
+    member (status, rank, stop, relres, dW, J, cv_num, cv_den, cv, pcg_iters,
+    cg_iters, seconds, slot); with ``keep`` also a list of ConReg handles on the
+    members' solved problems (the caller closes them).  Device memory comes from
+    the library's own allocator (the workers run outside Python)."""
+    import torch
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("solve_batch needs a CUDA device")
+    lib = load()
+    X = _f64(p.X)
+    Y = _f64(p.Y)
+    Om = np.asfortranarray(np.asarray(p.Omega, dtype=np.uint8))
+    hold = [X, Y, Om]
+    d = cr_problem_desc()
+    d.nx, d.ny, d.ninj = X.shape[0], Y.shape[0], X.shape[1]
+    for name, L in (("Lx", p.Lx), ("Ly", p.Ly)):
+        rp = np.ascontiguousarray(L.rowptr, dtype=np.int32)
+        co = np.ascontiguousarray(L.col, dtype=np.int32)
+        va = np.ascontiguousarray(L.val, dtype=np.float64)
+        hold += [rp, co, va]
+        setattr(d, name, cr_csr(L.n, _ptr(rp, _ip), _ptr(co, _ip), _ptr(va)))
+    d.X_host, d.ldx = _ptr(X), d.nx
+    d.Y_host, d.ldy = _ptr(Y), d.ny
+    d.Omega_host, d.ldo = _ptr(Om, _up), d.ny
+    d.lambda_ = 1.0
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    o = default_options(**opts)
+    o.stream = C.c_void_p(stream.cuda_stream)
+    n = len(members)
+    arr = (cr_member * max(n, 1))()
+    for k, (lam, fit, test) in enumerate(members):
+        fa = np.ascontiguousarray(fit, dtype=np.int32)
+        ta = np.ascontiguousarray(test if test is not None else [], dtype=np.int32)
+        hold += [fa, ta]
+        arr[k] = cr_member(float(lam), _ptr(fa, _ip), len(fa), _ptr(ta, _ip) if len(ta) else None, len(ta))
+    res = (cr_member_result * max(n, 1))()
+    handles = (C.c_void_p * max(n, 1))() if keep else None
+    st = lib.cr_solve_batch(C.byref(d), C.byref(o), arr, n, int(r_max), float(tau), float(relres_target),
+                            int(concurrency), res, handles)
+    out = []
+    for k in range(n):
+        r = res[k]
+        out.append({"status": r.status, "rank": r.rank, "stop": r.stop, "stop_name": STOP_NAMES.get(r.stop, "?"),
+                    "relres": r.relres, "dW": r.dW, "J": r.J, "cv_num": r.cv_num, "cv_den": r.cv_den,
+                    "cv": r.cv_num / r.cv_den if r.cv_den > 0 else float("nan"), "pcg_iters": r.pcg_iters,
+                    "cg_iters": r.cg_iters, "seconds": r.seconds, "slot": r.slot})
+    kept = []
+    if keep:
+        kept = [ConReg._adopt(handles[k], d.nx, d.ny, members[k][0]) if handles[k] else None for k in range(n)]
+    if st not in (CR_OK, CR_ENOTCONV):
+        for g in kept:
+            if g is not None:
+                g.close()
+        _check(st, None, "cr_solve_batch")
+    return (out, kept) if keep else out
 
 
 def cr_lambda_from_bar(lam_bar: float, ninj: int, nx: int) -> float:

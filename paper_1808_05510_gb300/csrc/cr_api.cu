@@ -56,6 +56,11 @@ namespace cr {
 void set_global_error(const std::string& msg) { g_create_err = msg; }
 }  // namespace cr
 
+struct cr_problem;
+namespace cr {
+cr_status adopt_stream(cr_problem* p, cudaStream_t st);
+}
+
 struct cr_problem {
   int nx = 0, ny = 0, m = 0, rcap = 0;
   double lam = 0.0;
@@ -94,6 +99,10 @@ struct cr_problem {
   float *net_in = nullptr, *net_out = nullptr;
   int64_t net_V = 0;
   double *fc_rold = nullptr, *fc_d = nullptr, *fc_t = nullptr, *fc_y = nullptr;
+  // held-out scoring (cr_cv_error): buffers for cv_cap columns
+  int cv_cap = 0;
+  double *cv_X = nullptr, *cv_Y = nullptr, *cv_T1 = nullptr, *cv_T2 = nullptr, *cv_P = nullptr, *cv_out = nullptr;
+  uint8_t* cv_Om = nullptr;
   int64_t fcg_fallbacks = 0, learned_solves = 0;
   // Jacobi as judge of the learned preconditioner, per side: the iteration count of
   // a Jacobi-PCG solve (0 = not measured yet), consecutive fallbacks, and whether
@@ -1075,6 +1084,21 @@ cr_status do_rank_one(cr_problem* p, cr_rank1_info* info) {
 
 }  // namespace
 
+namespace cr {
+// Move a problem onto stream st (NULL: a new library-owned stream) once the
+// work on its current stream has finished; the old stream is released if the
+// problem owned it.
+cr_status adopt_stream(cr_problem* p, cudaStream_t st) {
+  CUCHK(p, cudaStreamSynchronize(p->st));
+  cudaStream_t ns = st;
+  if (!ns) CUCHK(p, cudaStreamCreateWithFlags(&ns, cudaStreamNonBlocking));
+  if (p->own_stream && p->st) cudaStreamDestroy(p->st);
+  p->st = ns;
+  p->own_stream = !st;
+  return CR_OK;
+}
+}  // namespace cr
+
 // =========================================================================== C ABI
 extern "C" {
 
@@ -1309,6 +1333,7 @@ cr_status cr_create(const cr_problem_desc* d, const cr_options* o, cr_problem** 
   CK(dalloc(p, &p->cvec, (size_t)3 * rc + 2 * m));
   CK(dalloc(p, &p->coef, 8));
   p->gal_nb = galerkin_grid_size();
+  if (p->opt.galerkin_ctas > 0) p->gal_nb = std::min(p->gal_nb, (int)p->opt.galerkin_ctas);
   CK(dalloc(p, &p->gpart, (size_t)4 * std::max(1, p->gal_nb)));
   CK(dalloc(p, &p->gout, 4));
   CK(dalloc(p, &p->gbar, 2));
@@ -1638,6 +1663,52 @@ cr_status cr_set_factors(cr_problem* p, int32_t j, const double* U, int64_t ldu,
   build_F(p);
   refresh_E(p);
   return sync(p);
+}
+
+cr_status cr_cv_error(cr_problem* p, int32_t mt, const double* Xt, int64_t ldx, const double* Yt, int64_t ldy,
+                      const uint8_t* Omt, int64_t ldo, double* num, double* den) {
+  if (!p || !num || !den || mt < 0) return CR_EINVAL;
+  *num = *den = 0.0;
+  if (mt == 0) return CR_OK;
+  if (!Xt || !Yt || !Omt || ldx < p->nx || ldy < p->ny || ldo < p->ny) return fail(p, CR_EINVAL, "held-out data");
+  const int nx = p->nx, ny = p->ny, j = p->j;
+  cudaStream_t st = p->st;
+  if (mt > p->cv_cap) {
+    const int c = std::max(mt, 2 * p->cv_cap);
+    TRY(dalloc(p, &p->cv_X, (size_t)nx * c));
+    TRY(dalloc(p, &p->cv_Y, (size_t)ny * c));
+    TRY(dalloc(p, &p->cv_P, (size_t)ny * c));
+    TRY(dalloc(p, &p->cv_T1, (size_t)p->rcap * c));
+    TRY(dalloc(p, &p->cv_T2, (size_t)p->rcap * c));
+    TRY(dalloc(p, &p->cv_Om, (size_t)ny * c));
+    if (!p->cv_out) TRY(dalloc(p, &p->cv_out, 2));
+    p->cv_cap = c;
+  }
+  CUCHK(p, cudaMemcpy2DAsync(p->cv_X, nx * sizeof(double), Xt, ldx * sizeof(double), nx * sizeof(double), mt,
+                             cudaMemcpyHostToDevice, st));
+  CUCHK(p, cudaMemcpy2DAsync(p->cv_Y, ny * sizeof(double), Yt, ldy * sizeof(double), ny * sizeof(double), mt,
+                             cudaMemcpyHostToDevice, st));
+  CUCHK(p, cudaMemcpy2DAsync(p->cv_Om, ny, Omt, ldo, ny, mt, cudaMemcpyHostToDevice, st));
+  p->h2d_bytes += (int64_t)mt * (nx * 8 + ny * 9);
+  if (j == 0) {
+    fill((int64_t)ny * mt, 0.0, p->cv_P, st);
+  } else {
+    // T1 = V^T X_t (j x mt), T2 = Z T1, P = U T2 (U, V: column p at 3p of the interleaved panels)
+    gemm(j, mt, nx, 1.0, MatView{p->VV, 3 * (int64_t)nx, 1}, MatView{p->cv_X, 1, nx}, 0.0, p->cv_T1, 1, j, p->ws,
+         p->ws_elems, st);
+    gemm(j, mt, j, 1.0, MatView{p->Z, 1, p->rcap}, MatView{p->cv_T1, 1, j}, 0.0, p->cv_T2, 1, j, p->ws, p->ws_elems,
+         st);
+    gemm(ny, mt, j, 1.0, MatView{p->UU, 1, 3 * (int64_t)ny}, MatView{p->cv_T2, 1, j}, 0.0, p->cv_P, 1, ny, p->ws,
+         p->ws_elems, st);
+  }
+  cv_err(ny, mt, p->cv_P, p->cv_Y, p->cv_Om, p->cv_out, st);
+  double out[2] = {0.0, 0.0};
+  CUCHK(p, cudaMemcpyAsync(out, p->cv_out, sizeof(out), cudaMemcpyDeviceToHost, st));
+  p->d2h_bytes += (int64_t)sizeof(out);
+  TRY(sync(p));
+  *num = out[0];
+  *den = out[1];
+  return CR_OK;
 }
 
 cr_status cr_apply_residual(cr_problem* p, int32_t trans, const double* in, double* out) {

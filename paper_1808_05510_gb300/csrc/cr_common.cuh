@@ -202,6 +202,8 @@ void mask_residual(int n, int m, const double* OmY, const uint8_t* Om, int64_t l
 void omega_times(int n, int m, const uint8_t* Om, int64_t ldo, const double* u, double* B, cudaStream_t st);
 // out[0] = sum_{i<r, l<c} A(i,l) B(i,l) (single deterministic reduction)
 void mat_dot(int r, int c, const double* A, int64_t lda, const double* B, int64_t ldb, double* out, cudaStream_t st);
+// out[0] = sum Om (P - Y)^2, out[1] = sum Om Y^2 over n x m (P, Y, Om contiguous, ld n)
+void cv_err(int n, int m, const double* P, const double* Y, const uint8_t* Om, double* out, cudaStream_t st);
 // out[0] = |Z - Zp|_F^2, out[1] = |Z|_F^2 over j x j
 void mat_diff_norms(int j, const double* Z, const double* Zp, int64_t ld, double* out, cudaStream_t st);
 // C = alpha A + beta B (r x c); B may alias C

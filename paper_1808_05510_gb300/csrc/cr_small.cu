@@ -103,6 +103,20 @@ __global__ void mat_diff_kernel(int j, const double* __restrict__ Z, const doubl
   block_sum_store<2>(v, out);
 }
 
+// out[0] = sum Om (P - Y)^2, out[1] = sum Om Y^2 over n x m (Om is 0/1)
+__global__ void cv_err_kernel(int n, int m, const double* __restrict__ P, const double* __restrict__ Y,
+                              const uint8_t* __restrict__ Om, double* out) {
+  double v[2] = {0.0, 0.0};
+  const int64_t tot = (int64_t)n * m;
+  for (int64_t t = threadIdx.x; t < tot; t += blockDim.x) {
+    if (!Om[t]) continue;
+    const double y = Y[t], d = P[t] - y;
+    v[0] = fma(d, d, v[0]);
+    v[1] = fma(y, y, v[1]);
+  }
+  block_sum_store<2>(v, out);
+}
+
 __global__ void mat_axpby_kernel(int r, int c, double alpha, const double* A, int64_t lda, double beta,
                                  const double* B, int64_t ldb, double* C, int64_t ldc) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -194,6 +208,11 @@ void omega_times(int n, int m, const uint8_t* Om, int64_t ldo, const double* u, 
 void mat_dot(int r, int c, const double* A, int64_t lda, const double* B, int64_t ldb, double* out, cudaStream_t st) {
   count_launch();
   mat_dot_kernel<<<1, 1024, 0, st>>>(r, c, A, lda, B, ldb, out);
+}
+
+void cv_err(int n, int m, const double* P, const double* Y, const uint8_t* Om, double* out, cudaStream_t st) {
+  count_launch();
+  cv_err_kernel<<<1, 1024, 0, st>>>(n, m, P, Y, Om, out);
 }
 
 void mat_diff_norms(int j, const double* Z, const double* Zp, int64_t ld, double* out, cudaStream_t st) {

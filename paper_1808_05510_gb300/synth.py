@@ -27,7 +27,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
-from typing import Optional
+from typing import List, Optional, Tuple
 
 import numpy as np
 
@@ -297,6 +297,53 @@ def whole_cortex(seed: int = 1811, shape=(96, 64, 80), n_target: int = 45000, m:
     g = Grid(shell_mask(shape, n_target))
     X = gaussian_injections(g, m, rng, 2.0, 5.0, 0.2, 1.0)
     return _finish(f"cortex-{g.n}vox-m{m}", g, g, X, rng, lam, r_max, sparse_cut=1e-3)
+
+
+def sweep_cortex(seed: int = 1814, box: int = 40, n_target: int = 15000, m: int = 126, lam: float = 1e2,
+                 r_max: int = 200) -> Problem:
+    """Data set of the lambda x fold sweep: the visual-cortex recipe on ~15,000
+    voxels of a 40^3 box with 126 injections (each sweep member fits a subset)."""
+    rng = np.random.default_rng(seed)
+    g = Grid(blob_mask((box, box, box), n_target, rng))
+    X = gaussian_injections(g, m, rng, 2.0, 2.0, 1.0, 1.0)
+    return _finish(f"sweep-{g.n}vox-m{m}", g, g, X, rng, lam, r_max)
+
+
+def fold_partition(m: int, k: int = 5, lo: int = 20, hi: int = 30, seed: int = 1815) -> List[np.ndarray]:
+    """Seeded partition of the injections 0..m-1 into k folds whose sizes lie in
+    [lo, hi] (uneven: the sizes are drawn, not equal)."""
+    if not (k * lo <= m <= k * hi):
+        raise ValueError("no partition with these fold sizes")
+    rng = np.random.default_rng(seed)
+    sizes = np.full(k, lo)
+    for _ in range(m - k * lo):
+        room = np.flatnonzero(sizes < hi)
+        sizes[rng.choice(room)] += 1
+    perm = rng.permutation(m)
+    cuts = np.concatenate([[0], np.cumsum(sizes)])
+    return [np.sort(perm[cuts[f]:cuts[f + 1]]) for f in range(k)]
+
+
+def lambda_grid(count: int = 16, lo: float = 1e0, hi: float = 1e6) -> np.ndarray:
+    """Log-spaced lambda values of the sweep."""
+    return np.logspace(np.log10(lo), np.log10(hi), count)
+
+
+def sweep_members(m: int, lams, folds) -> List[Tuple[float, np.ndarray, np.ndarray]]:
+    """(lambda, fit columns, held-out columns) for every lambda x fold pair."""
+    out = []
+    for lam in lams:
+        for test in folds:
+            fit = np.setdiff1d(np.arange(m), test)
+            out.append((float(lam), fit, np.asarray(test)))
+    return out
+
+
+def member_problem(p: Problem, lam: float, fit) -> Problem:
+    """The sub-problem a sweep member solves: the fit columns of X, Y, Omega with its lambda."""
+    fit = np.asarray(fit)
+    return dataclasses.replace(p, name=f"{p.name}-lam{lam:g}-fit{len(fit)}", X=p.X[:, fit], Y=p.Y[:, fit],
+                               Omega=p.Omega[:, fit], lam=float(lam))
 
 
 def rect2d(seed: int = 1812, shape_y=(9, 7), shape_x=(6, 8), m: int = 4, lam: float = 3.0, r_max: int = 12,
