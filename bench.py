@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-r", type=int, default=8, help="rank of every sweep member in the batched form")
     ap.add_argument("--learn-steps", type=int, default=200)
     return ap.parse_args()
 
@@ -316,6 +318,8 @@ def run_ours(args, rank, world, local_rank):
                           "problems": "2 visual-cortex-shaped problems, seeds 1900-1901, ranks 0/5/10, both sides"}
         forms["learned"] = lf
         net.close()
+    if not args.no_batch:
+        forms["batched"] = measure_batch(args)
     head = forms[args.precision]
     hbm, peak_kind = peaks()
     roofline = {"bound": "hbm", "achieved": head["pcg"]["achieved"], "peak": hbm, "unit": "GB/s",
@@ -364,6 +368,50 @@ def run_ours(args, rank, world, local_rank):
         out["cpu_baseline"] = oracle_sample(p, args, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def measure_batch(args):
+    """Batched form: the lambda x fold sweep (16 lambdas log-spaced 1..1e6 x 5 folds
+    of a 126-injection, ~15,000-voxel data set; every member fits 96-106
+    injections) in the mixed form, after the autotuner picked its launch shape.
+    Beside it, one member at a time (concurrency 1) on a 16-member sample, one
+    member per lambda, to show what running members side by side gains."""
+    import torch
+    from paper_1808_05510_gb300 import sweep, synth as _synth
+    from paper_1808_05510_gb300.conreg import CR_MIXED, solve_batch
+
+    t0 = time.perf_counter()
+    bp = _synth.sweep_cortex()
+    folds = _synth.fold_partition(bp.m)
+    mem = _synth.sweep_members(bp.m, _synth.lambda_grid(), folds)
+    gen_s = time.perf_counter() - t0
+    solve_batch(bp, mem[:9], r_max=2, tau=args.tau, precision=CR_MIXED)  # warm-up
+    shape = sweep.autotune(bp, mem, r_probe=2, tau=args.tau, precision=CR_MIXED)
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        res, sec = sweep._timed_batch(bp, mem, args.batch_r, tau=args.tau, relres_target=args.relres,
+                                      concurrency=shape["concurrency"], cluster_size=shape["cluster_size"],
+                                      precision=CR_MIXED)
+    ranks = sum(r["rank"] for r in res)
+    sample = mem[::5]
+    seq, seq_sec = sweep._timed_batch(bp, sample, args.batch_r, tau=args.tau, relres_target=args.relres,
+                                      concurrency=1, precision=CR_MIXED)
+    seq_ranks = sum(r["rank"] for r in seq)
+    cv = sweep.cv_summary(mem, res)
+    status = {}
+    for r in res:
+        status[str(r["status"])] = status.get(str(r["status"]), 0) + 1
+    torch.cuda.synchronize()
+    return {"value": ranks / sec, "unit": UNIT + " (aggregate over members)", "seconds": sec,
+            "members": len(mem), "voxels": bp.nx, "ninj_total": bp.m,
+            "ninj_fit": sorted({len(f) for _, f, _ in mem}), "r_max": args.batch_r, "precision": "mixed",
+            "ranks": ranks, "shape": {k: shape[k] for k in ("concurrency", "cluster_size")},
+            "autotune": shape["table"], "status_counts": status,
+            "sequential_sample": {"members": len(sample), "seconds": seq_sec, "value": seq_ranks / seq_sec},
+            "speedup_vs_sequential": (ranks / sec) / (seq_ranks / seq_sec),
+            "pcg_iters": sum(r["pcg_iters"] for r in res), "galerkin_cg_iters": sum(r["cg_iters"] for r in res),
+            "best_lambda": cv["best_lambda"], "cv_by_lambda": {f"{k:.3g}": v for k, v in cv["cv_by_lambda"].items()},
+            "final_relres_range": [min(r["relres"] for r in res), max(r["relres"] for r in res)],
+            "data_gen_s": gen_s, "clocks": clk.summary()}
 
 
 def main():

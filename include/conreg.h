@@ -44,6 +44,12 @@ typedef enum {
   CR_ESTATE = 7     /* call not valid in the current state (e.g. rank capacity reached) */
 } cr_status;
 
+/* CR_FP64: every step in float64.  CR_MIXED: the u/v sub-solves run float32
+ * PCG (double-float inner products) inside float64 iterative refinement to the
+ * same pcg_tol as CR_FP64 (handing over to the float64 kernel when float32
+ * cannot resolve the system); the Galerkin solve runs a float32 inner CG,
+ * with BF16 tensor-core assembly of the G_a, inside float64 refinement; the
+ * residual norm and stopping test stay float64. */
 typedef enum { CR_FP64 = 0, CR_MIXED = 1 } cr_precision;
 typedef enum { CR_PRECOND_JACOBI = 0, CR_PRECOND_LEARNED = 1 } cr_precond;
 typedef enum { CR_STOP_NONE = 0, CR_STOP_RMAX = 1, CR_STOP_DW = 2, CR_STOP_RELRES = 3, CR_STOP_RANK = 4 } cr_stop;
@@ -153,6 +159,7 @@ typedef struct {
   int64_t learned_solves;         /* sub-solves finished by the learned flexible CG */
   int64_t learned_fallbacks;      /* learned solves that stagnated and were finished by Jacobi-PCG */
   int64_t learned_off;            /* bit s set: the learned form is switched off for side s */
+  int64_t mixed_handovers;        /* mixed-form sub-solves that float32 refinement handed to float64 */
 } cr_stats;
 
 /* Fill *o with defaults (struct_size set).  Always succeeds for o != NULL. */

@@ -69,7 +69,8 @@ PHASES = ["pcg_u", "pcg_v", "rhs", "orth", "galerkin", "resid", "p6", "p7"]
 class cr_stats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("pcg_solves", C.c_int64), ("pcg_iters", C.c_int64),
                 ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("phase_ms", C.c_double * 8), ("phase_calls", C.c_int64 * 8),
-                ("learned_solves", C.c_int64), ("learned_fallbacks", C.c_int64), ("learned_off", C.c_int64)]
+                ("learned_solves", C.c_int64), ("learned_fallbacks", C.c_int64), ("learned_off", C.c_int64),
+                ("mixed_handovers", C.c_int64)]
 
 
 class cr_solve_info(C.Structure):
@@ -383,7 +384,7 @@ class ConReg:
                 "phase_ms": {PHASES[i]: s.phase_ms[i] for i in range(8)},
                 "phase_calls": {PHASES[i]: s.phase_calls[i] for i in range(8)},
                 "learned_solves": s.learned_solves, "learned_fallbacks": s.learned_fallbacks,
-                "learned_off": s.learned_off}
+                "learned_off": s.learned_off, "mixed_handovers": s.mixed_handovers}
 
     def cr_solve_u(self, v, rhs):
         v = np.ascontiguousarray(v, dtype=np.float64)

@@ -38,11 +38,15 @@ using namespace cr;
 namespace {
 thread_local std::string g_create_err;
 
-constexpr double kMixedPcgTol = 1e-6;
+// Mixed form: relative residual each float32 inner PCG solve of a refinement
+// step aims for (float32 vectors resolve little below 1e-6), and the cap on
+// refinement steps before the float64 kernel takes over.
+constexpr double kMixedInnerTol = 1e-5;
+constexpr int kMaxRefine = 8;
 
 enum {
   DS_UN2 = 0, DS_VN2 = 1, DS_NB = 2, DS_NA = 3, DS_DW = 4, /*5*/ DS_ZKZ = 6, DS_ZF = 7, DS_RN = 8, DS_V0 = 9,
-  DS_GS = 16, DS_FCG = 24, DS_COUNT = 32
+  DS_GS = 16, DS_FCG = 24, DS_REF = 30, DS_COUNT = 32
 };
 
 struct HostScal {
@@ -103,7 +107,7 @@ struct cr_problem {
   int cv_cap = 0;
   double *cv_X = nullptr, *cv_Y = nullptr, *cv_T1 = nullptr, *cv_T2 = nullptr, *cv_P = nullptr, *cv_out = nullptr;
   uint8_t* cv_Om = nullptr;
-  int64_t fcg_fallbacks = 0, learned_solves = 0;
+  int64_t fcg_fallbacks = 0, learned_solves = 0, mixed_handovers = 0;
   // Jacobi as judge of the learned preconditioner, per side: the iteration count of
   // a Jacobi-PCG solve (0 = not measured yet), consecutive fallbacks, and whether
   // the learned form has been switched off for this side
@@ -502,6 +506,7 @@ void prep_v(cr_problem* p, const double* uu) {
 }
 
 cr_status launch_pcg_jacobi(cr_problem* p, int side, const double* b, double* x, int maxit);
+cr_status launch_pcg_mixed(cr_problem* p, int side, const double* b, double* x, int maxit);
 
 // Flexible CG (Polak-Ribiere) with the learned preconditioner
 // z = D^-1 r + s net(D^-1 r / s, mask); float64 vectors.  If it has not
@@ -514,7 +519,7 @@ cr_status fcg_learned(cr_problem* p, int side, const double* b, double* x) {
   const double* coef = p->coef + (side == 0 ? 0 : 2);
   double* sc = p->ds + DS_FCG;
   double *r = p->pr, *q = p->pw, *pv = p->pp, *z = p->ps, *rold = p->fc_rold, *dd = p->fc_d, *t = p->fc_t;
-  const double tol = p->opt.precision == CR_MIXED ? std::max(p->opt.pcg_tol, kMixedPcgTol) : p->opt.pcg_tol;
+  const double tol = p->opt.pcg_tol;
   prof_begin(p, side == 0 ? CR_PHASE_PCG_U : CR_PHASE_PCG_V);
   fcg_jacobi_diag(L, p->lam, coef, side, p->m, p->Om, p->ny, p->xi, p->xl, p->svec, p->pomt, p->pdinv, st);
   fcg_apply(L, p->lam, coef, side, p->pomt, p->xl, p->xc_ptr, p->xc_row, p->xc_val, p->m, p->svec, p->fc_y, x, t, q,
@@ -582,7 +587,7 @@ cr_status launch_pcg(cr_problem* p, int side, const double* b, double* x) {
   return launch_pcg_jacobi(p, side, b, x, p->opt.pcg_maxit);
 }
 
-cr_status launch_pcg_jacobi(cr_problem* p, int side, const double* b, double* x, int maxit) {
+PcgArgs pcg_args(cr_problem* p, int side, const double* b, double* x, int maxit, double tol, bool fp32) {
   PcgArgs a{};
   a.lam = p->lam;
   a.m = p->m;
@@ -594,10 +599,8 @@ cr_status launch_pcg_jacobi(cr_problem* p, int side, const double* b, double* x,
   a.w = p->pw;
   a.dinv = p->pdinv;
   a.omt = p->pomt;
-  // The mixed form runs the sub-solves in float32 (inner products in float64);
-  // float32 vectors cannot resolve relative residuals much below 1e-6.
-  a.fp32 = p->opt.precision == CR_MIXED;
-  a.tol = a.fp32 ? std::max(p->opt.pcg_tol, kMixedPcgTol) : p->opt.pcg_tol;
+  a.fp32 = fp32;
+  a.tol = tol;
   a.maxit = maxit;
   a.stat = p->stat + side;
   a.force_generic = p->opt.pcg_kernel == 1;
@@ -613,9 +616,75 @@ cr_status launch_pcg_jacobi(cr_problem* p, int side, const double* b, double* x,
     a.X = p->xl;
     a.s = p->svec;
   }
+  return a;
+}
+
+// Jacobi PCG on Eq. (ALS_linsys) (side 0) or Eq. (ALS_linsys_v) (side 1):
+// float64 form, or the mixed form's float64 refinement around float32 solves.
+cr_status launch_pcg_jacobi(cr_problem* p, int side, const double* b, double* x, int maxit) {
+  if (p->opt.precision == CR_MIXED) return launch_pcg_mixed(p, side, b, x, maxit);
   prof_begin(p, side == 0 ? CR_PHASE_PCG_U : CR_PHASE_PCG_V);
-  CUCHK(p, pcg_launch(a, side, p->st));
+  CUCHK(p, pcg_launch(pcg_args(p, side, b, x, maxit, p->opt.pcg_tol, false), side, p->st));
   prof_end(p, side == 0 ? CR_PHASE_PCG_U : CR_PHASE_PCG_V);
+  return CR_OK;
+}
+
+// Mixed form of the sub-solves: float64 iterative refinement around the
+// float32 cluster PCG.  Each outer step forms the float64 residual
+// r = b - A_hat x, stops once |r| <= pcg_tol |b|, and otherwise solves
+// A_hat d = r from d = 0 in float32 (inner products in double-float) to
+// kMixedInnerTol relative, then x += d.  An outer step that does not cut |r|
+// by 4x (float32 cannot resolve the system, e.g. at very large lambda) or the
+// step cap hands the solve over to the float64 kernel from the current x, so
+// the result meets the float64 tolerance either way.
+cr_status launch_pcg_mixed(cr_problem* p, int side, const double* b, double* x, int maxit) {
+  cudaStream_t st = p->st;
+  const DevLap& L = side == 0 ? p->Ly : p->Lx;
+  const int n = L.n;
+  const double* coef = p->coef + (side == 0 ? 0 : 2);
+  double* sc = p->ds + DS_REF;
+  double *r = p->fc_rold, *d = p->fc_d, *q = p->pw;
+  const double tol = p->opt.pcg_tol;
+  prof_begin(p, side == 0 ? CR_PHASE_PCG_U : CR_PHASE_PCG_V);
+  fcg_jacobi_diag(L, p->lam, coef, side, p->m, p->Om, p->ny, p->xi, p->xl, p->svec, p->pomt, p->pdinv, st);
+  dot(n, b, b, sc + 0, st);
+  PcgStat hs{0, 0, 0.0, 0.0};
+  int total = 0;
+  double rr_prev = INFINITY;
+  for (int outer = 0;; ++outer) {
+    fcg_apply(L, p->lam, coef, side, p->pomt, p->xl, p->xc_ptr, p->xc_row, p->xc_val, p->m, p->svec, p->fc_y, x,
+              p->fc_t, q, st);
+    mat_axpby(n, 1, 1.0, b, n, -1.0, q, n, r, n, st);  // r = b - A x (float64)
+    dot(n, r, r, sc + 1, st);
+    TRY(readback(p, DS_REF, 2, false));
+    const double bb = p->hs->ds[DS_REF], rr = p->hs->ds[DS_REF + 1];
+    hs.bnorm = std::sqrt(bb);
+    hs.relres = bb > 0.0 ? std::sqrt(rr / bb) : 0.0;
+    if (!(bb > 0.0) || rr <= tol * tol * bb) break;
+    if (outer >= kMaxRefine || !(rr < 0.25 * rr_prev) || total >= maxit) {
+      // hand over to the float64 kernel from the current iterate
+      p->mixed_handovers += 1;
+      CUCHK(p, pcg_launch(pcg_args(p, side, b, x, std::max(1, maxit - total), tol, false), side, st));
+      TRY(readback(p, 0, 1, true));
+      hs = p->hs->stat[side];
+      hs.iters += total;
+      break;
+    }
+    rr_prev = rr;
+    fill(n, 0.0, d, st);
+    CUCHK(p, pcg_launch(pcg_args(p, side, r, d, maxit - total, kMixedInnerTol, true), side, st));
+    TRY(readback(p, 0, 1, true));
+    const PcgStat in = p->hs->stat[side];
+    total += in.iters;
+    hs.iters = total;
+    if (in.status == 2) {
+      hs.status = 2;
+      break;
+    }
+    mat_axpby(n, 1, 1.0, d, n, 1.0, x, n, x, n, st);  // x += d
+  }
+  prof_end(p, side == 0 ? CR_PHASE_PCG_U : CR_PHASE_PCG_V);
+  CUCHK(p, cudaMemcpyAsync(p->stat + side, &hs, sizeof(PcgStat), cudaMemcpyHostToDevice, st));
   return CR_OK;
 }
 
@@ -1542,6 +1611,7 @@ cr_status cr_get_stats(cr_problem* p, cr_stats* s, int32_t reset) {
   s->learned_solves = p->learned_solves;
   s->learned_fallbacks = p->fcg_fallbacks;
   s->learned_off = (p->learned_off[0] ? 1 : 0) | (p->learned_off[1] ? 2 : 0);
+  s->mixed_handovers = p->mixed_handovers;
   for (int i = 0; i < CR_NPHASE; ++i) {
     s->phase_ms[i] = p->phase_ms[i];
     s->phase_calls[i] = p->phase_calls[i];
@@ -1550,7 +1620,7 @@ cr_status cr_get_stats(cr_problem* p, cr_stats* s, int32_t reset) {
     p->launch_base = cr::g_launches.load();
     p->pcg_solves = p->pcg_iters = 0;
     p->h2d_bytes = p->d2h_bytes = 0;
-    p->learned_solves = p->fcg_fallbacks = 0;
+    p->learned_solves = p->fcg_fallbacks = p->mixed_handovers = 0;
     for (int i = 0; i < CR_NPHASE; ++i) {
       p->phase_ms[i] = 0.0;
       p->phase_calls[i] = 0;

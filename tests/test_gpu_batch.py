@@ -95,3 +95,19 @@ def test_batch_edge_cases(cr, data):
         cr.solve_batch(p, [(lam, np.array([0, 99]), None)], r_max=2)
     with pytest.raises(cr.ConRegError):
         cr.solve_batch(p, [(-1.0, fit, None)], r_max=2)
+
+
+def test_autotune_and_cv_summary(cr, data):
+    from paper_1808_05510_gb300 import sweep
+
+    p, members = data
+    cands = ((1, 16), (3, 8))
+    shape = sweep.autotune(p, members, r_probe=1, candidates=cands)
+    assert (shape["concurrency"], shape["cluster_size"]) in cands and len(shape["table"]) == 2
+    out = sweep.run(p, members, r_max=2, tune=False)
+    curve = out["cv_by_lambda"]
+    assert set(curve) == {m[0] for m in members}
+    lam = members[0][0]
+    rs = [r for m, r in zip(members, out["results"]) if m[0] == lam]
+    assert abs(curve[lam] - sum(r["cv_num"] for r in rs) / sum(r["cv_den"] for r in rs)) <= 1e-15 * curve[lam]
+    assert out["best_lambda"] == min(curve, key=curve.get)
