@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-ttr", action="store_true")
     ap.add_argument("--batch-r", type=int, default=8, help="rank of every sweep member in the batched form")
     ap.add_argument("--learn-steps", type=int, default=200)
     return ap.parse_args()
@@ -280,12 +281,16 @@ def run_ours(args, rank, world, local_rank):
         value = float(r_local.item()) / (t_max / 1e3)
         reached = [i for i in infos if i["stop_name"] == "relres"]
         ttr = (sum(m for m, i in zip(ms, infos) if i["stop_name"] == "relres") / len(reached) / 1e3) if reached else None
+        # the PCG kernel's own launches (CUDA events around each launch, on the
+        # problem's stream); the mixed form's sub-solves are several float32
+        # launches inside float64 refinement
         pcg_ms = stats["phase_ms"]["pcg_u"] + stats["phase_ms"]["pcg_v"]
-        pcg_calls = stats["phase_calls"]["pcg_u"] + stats["phase_calls"]["pcg_v"]
-        iters_per_launch = stats["pcg_iters"] / max(1, stats["pcg_solves"])
+        kern_ms = stats["phase_ms"]["pcg_kernel"]
+        kern_calls = max(1, stats["phase_calls"]["pcg_kernel"])
+        iters_per_launch = stats["pcg_iters"] / kern_calls
         word = 8.0 if prec == CR_FP64 else 4.0
         bytes_per_launch = iters_per_launch * pcg_bytes_per_iter(int(0.5 * (p.nx + p.ny)), word=word)
-        avg_launch_s = pcg_ms / max(1, pcg_calls) / 1e3
+        avg_launch_s = kern_ms / kern_calls / 1e3
         achieved = bytes_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
         return {"value": value, "ms_per_step": t_max / steps, "steps": steps, "time_to_relres_s": ttr,
                 "relres_reached_steps": len(reached), "final_relres": infos[-1]["relres"],
@@ -296,7 +301,8 @@ def run_ours(args, rank, world, local_rank):
                 "gpu_launches": stats["launches"], "clocks": clk.summary(),
                 "pcg": {"achieved": achieved, "avg_launch_us": avg_launch_s * 1e6, "iters_per_launch": iters_per_launch,
                         "us_per_iter": avg_launch_s * 1e6 / max(iters_per_launch, 1e-9),
-                        "share_of_step": pcg_ms / tot_ms if tot_ms > 0 else None},
+                        "share_of_step": pcg_ms / tot_ms if tot_ms > 0 else None,
+                        "kernel_share_of_step": kern_ms / tot_ms if tot_ms > 0 else None},
                 **({"judge": {"learned_solves": stats["learned_solves"], "fallbacks": stats["learned_fallbacks"],
                               "switched_off_sides": [s for s in (0, 1) if stats["learned_off"] >> s & 1]}}
                    if net is not None else {})}
@@ -320,12 +326,14 @@ def run_ours(args, rank, world, local_rank):
         net.close()
     if not args.no_batch:
         forms["batched"] = measure_batch(args)
+    ttr_toy = None if args.no_ttr else measure_ttr_toy(args)
     head = forms[args.precision]
     hbm, peak_kind = peaks()
     roofline = {"bound": "hbm", "achieved": head["pcg"]["achieved"], "peak": hbm, "unit": "GB/s",
                 "frac": head["pcg"]["achieved"] / hbm, "traffic": pcg_traffic(args.precision),
                 "kernel": "pcg_reg_kernel (cluster PCG)",
                 "peak_kind": peak_kind, "pcg_share_of_step": head["pcg"]["share_of_step"],
+                "kernel_share_of_step": head["pcg"]["kernel_share_of_step"],
                 "avg_launch_us": head["pcg"]["avg_launch_us"], "iters_per_launch": head["pcg"]["iters_per_launch"],
                 "us_per_iter": head["pcg"]["us_per_iter"]}
     out = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -334,6 +342,7 @@ def run_ours(args, rank, world, local_rank):
            "config": cfg, "time_to_relres_s": head["time_to_relres_s"], "final_relres": head["final_relres"],
            "final_rank": head["final_rank"], "stop": head["stop"],
            "speedup_vs_fp64": head["value"] / forms["fp64"]["value"],
+           "time_to_relres_toy": ttr_toy,
            "roofline": roofline, "gpu_launches": head["gpu_launches"], "clocks": head["clocks"],
            "forms": {k: {kk: vv for kk, vv in v.items() if kk not in ("clocks",)} for k, v in forms.items()}}
     prec_e2e = CR_MIXED if args.precision == "mixed" else CR_FP64
@@ -368,6 +377,39 @@ def run_ours(args, rank, world, local_rank):
         out["cpu_baseline"] = oracle_sample(p, args, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def measure_ttr_toy(args, runs: int = 3):
+    """Time to relative residual 1e-6 on the toy workload (20 x 20 grid, 5
+    injections, lambda = 100), where the greedy reaches it (near rank 90): CUDA
+    events around cr_solve from a freshly created problem (creation untimed),
+    residual checked every step, median of `runs` after one warm-up."""
+    import numpy as np
+    import torch
+    from paper_1808_05510_gb300 import synth as _synth
+    from paper_1808_05510_gb300.conreg import CR_FP64, CR_MIXED, ConReg
+
+    tp = _synth.toy2d()
+    stream = torch.cuda.current_stream()
+    out = {"workload": "toy 20x20 grid, 5-point Laplacian, 5 injections, lambda 100, rank cap 400",
+           "target": 1e-6}
+    for name, prec in (("fp64", CR_FP64), ("mixed", CR_MIXED)):
+        times, info = [], None
+        for k in range(runs + 1):
+            with ConReg.from_problem(tp, r_cap=400, precision=prec) as g:
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                info = g.cr_solve(400, 1e-13, 1e-6)
+                e1.record(stream)
+                e1.synchronize()
+                if k:
+                    times.append(e0.elapsed_time(e1) / 1e3)
+        out[name] = {"seconds": float(np.median(times)), "rank": info["rank"], "relres": info["relres"],
+                     "stop": info["stop_name"]}
+    out["mixed_speedup"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    return out
 
 
 def measure_batch(args):

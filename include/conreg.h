@@ -99,7 +99,9 @@ typedef struct {
   int32_t residual_every;  /* cr_solve: evaluate ‖R‖_F every k steps (default 1) */
   int32_t cluster_size;    /* PCG thread-block cluster size; 0 = automatic */
   int32_t profile;         /* != 0: time each phase with CUDA events (see cr_get_stats) */
-  int32_t pcg_kernel;      /* 0 = automatic (register-resident kernel when it applies), 1 = generic kernel */
+  int32_t pcg_kernel;      /* 0 = automatic: the cluster-resident kernel (register-resident variant when it
+                              applies) while the grid fits one cluster's shared memory, else the grid-wide
+                              kernel; 1 = generic cluster kernel; 2 = always the grid-wide kernel */
   int32_t galerkin_kernel; /* 0 = one persistent cooperative launch per projection, 1 = one launch per step */
   uint64_t seed;           /* seed of the fallback ALS start vector */
   void* stream;            /* cudaStream_t for all device work; NULL = a library-owned stream */
@@ -146,6 +148,7 @@ typedef enum {
   CR_PHASE_ORTH = 3,     /* orthogonalisation and projected coefficient matrices */
   CR_PHASE_GALERKIN = 4, /* Galerkin CG on Eq. (Proj_Sylv) and the masked data residual */
   CR_PHASE_RESID = 5,    /* residual norm, objective, dW */
+  CR_PHASE_PCG_KERNEL = 6, /* the Jacobi-PCG kernel launches alone (inside PCG_U / PCG_V) */
   CR_NPHASE = 8
 } cr_phase;
 

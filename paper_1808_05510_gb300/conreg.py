@@ -63,7 +63,7 @@ class cr_proj_info(C.Structure):
     _fields_ = [("iters", C.c_int32), ("relres", C.c_double)]
 
 
-PHASES = ["pcg_u", "pcg_v", "rhs", "orth", "galerkin", "resid", "p6", "p7"]
+PHASES = ["pcg_u", "pcg_v", "rhs", "orth", "galerkin", "resid", "pcg_kernel", "p7"]
 
 
 class cr_stats(C.Structure):

@@ -108,6 +108,10 @@ struct cr_problem {
   double *cv_X = nullptr, *cv_Y = nullptr, *cv_T1 = nullptr, *cv_T2 = nullptr, *cv_P = nullptr, *cv_out = nullptr;
   uint8_t* cv_Om = nullptr;
   int64_t fcg_fallbacks = 0, learned_solves = 0, mixed_handovers = 0;
+  // grid-wide PCG (grids beyond one cluster, or pcg_kernel = 2): work buffers
+  double *pg_work = nullptr, *pg_part = nullptr, *pg_ypart = nullptr, *pg_yglob = nullptr;
+  unsigned* pg_bar = nullptr;
+  int* pg_err = nullptr;
   // Jacobi as judge of the learned preconditioner, per side: the iteration count of
   // a Jacobi-PCG solve (0 = not measured yet), consecutive fallbacks, and whether
   // the learned form has been switched off for this side
@@ -360,10 +364,10 @@ cr_status build_lap(cr_problem* p, const cr_csr& c, DevLap& L) {
       break;
     }
   }
-  if (cs == 0)
-    return fail(p, CR_EINVAL, "grid of " + std::to_string(n) +
-                                  " voxels does not fit the cluster-resident PCG (shared memory / cluster size)");
-  if (p->opt.cluster_size > 0 && p->opt.cluster_size < cs) {
+  if (cs == 0) {
+    // too large for one cluster: the sub-solves run on the grid-wide PCG
+    chunk = n;
+  } else if (p->opt.cluster_size > 0 && p->opt.cluster_size < cs) {
     const int c2 = p->opt.cluster_size;
     const int ch = (n + c2 - 1) / c2;
     if (pcg_smem_bytes(ch, p->m) <= smem_cap && pcg_cluster_ok(c2, pcg_smem_bytes(ch, p->m))) {
@@ -396,7 +400,7 @@ cr_status build_lap(cr_problem* p, const cr_csr& c, DevLap& L) {
   L.l2diag = dl2;
   L.chunk = chunk;
   L.csize = cs;
-  CUCHK(p, pcg_prepare(0, cs, pcg_smem_bytes(chunk, p->m)));
+  if (cs > 0) CUCHK(p, pcg_prepare(0, cs, pcg_smem_bytes(chunk, p->m)));
   return CR_OK;
 }
 
@@ -619,12 +623,54 @@ PcgArgs pcg_args(cr_problem* p, int side, const double* b, double* x, int maxit,
   return a;
 }
 
+bool use_grid_pcg(const cr_problem* p, int side) {
+  return p->opt.pcg_kernel == 2 || (side == 0 ? p->Ly.csize : p->Lx.csize) == 0;
+}
+
+// One Jacobi-PCG solve on the cluster-resident kernel, or on the grid-wide
+// kernel for grids beyond one cluster (that path waits for the result, to
+// turn a grid barrier timeout into CR_ETIMEOUT).
+cr_status run_pcg(cr_problem* p, int side, const double* b, double* x, int maxit, double tol, bool fp32) {
+  if (!use_grid_pcg(p, side)) {
+    prof_begin(p, CR_PHASE_PCG_KERNEL);
+    CUCHK(p, pcg_launch(pcg_args(p, side, b, x, maxit, tol, fp32), side, p->st));
+    prof_end(p, CR_PHASE_PCG_KERNEL);
+    return CR_OK;
+  }
+  const int nmax = std::max(p->nx, p->ny);
+  if (!p->pg_work) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int nbm = std::max(1, 2 * sms);  // the launcher keeps at most two blocks per SM
+    TRY(dalloc(p, &p->pg_work, pcg_grid_work_elems(nmax)));
+    TRY(dalloc(p, &p->pg_part, (size_t)4 * nbm));
+    TRY(dalloc(p, &p->pg_ypart, (size_t)nbm * std::max(1, p->m)));
+    TRY(dalloc(p, &p->pg_yglob, (size_t)std::max(1, p->m)));
+    TRY(dalloc(p, &p->pg_bar, 2));
+    TRY(dalloc(p, &p->pg_err, 1));
+  }
+  const DevLap& L = side == 0 ? p->Ly : p->Lx;
+  const int nb = pcg_grid_blocks(fp32, p->m, L.K);
+  if (nb < 1) return fail(p, CR_ECUDA, "the grid-wide PCG cannot be launched on this device");
+  const double* coef = p->coef + (side == 0 ? 0 : 2);
+  fcg_jacobi_diag(L, p->lam, coef, side, p->m, p->Om, p->ny, p->xi, p->xl, p->svec, p->pomt, p->pdinv, p->st);
+  PcgArgs a = pcg_args(p, side, b, x, maxit, tol, fp32);
+  prof_begin(p, CR_PHASE_PCG_KERNEL);
+  CUCHK(p, pcg_grid_launch(a, side, p->xc_ptr, p->xc_row, p->xc_val, p->pg_work, p->pg_part, p->pg_ypart,
+                           p->pg_yglob, p->pg_bar, p->pg_err, std::min(nb, std::max(1, L.n / 64)), p->st));
+  prof_end(p, CR_PHASE_PCG_KERNEL);
+  TRY(readback(p, 0, 1, true));
+  if (p->hs->stat[side].status == 3) return fail(p, CR_ETIMEOUT, "grid-wide PCG barrier timed out");
+  return CR_OK;
+}
+
 // Jacobi PCG on Eq. (ALS_linsys) (side 0) or Eq. (ALS_linsys_v) (side 1):
 // float64 form, or the mixed form's float64 refinement around float32 solves.
 cr_status launch_pcg_jacobi(cr_problem* p, int side, const double* b, double* x, int maxit) {
   if (p->opt.precision == CR_MIXED) return launch_pcg_mixed(p, side, b, x, maxit);
   prof_begin(p, side == 0 ? CR_PHASE_PCG_U : CR_PHASE_PCG_V);
-  CUCHK(p, pcg_launch(pcg_args(p, side, b, x, maxit, p->opt.pcg_tol, false), side, p->st));
+  TRY(run_pcg(p, side, b, x, maxit, p->opt.pcg_tol, false));
   prof_end(p, side == 0 ? CR_PHASE_PCG_U : CR_PHASE_PCG_V);
   return CR_OK;
 }
@@ -664,7 +710,7 @@ cr_status launch_pcg_mixed(cr_problem* p, int side, const double* b, double* x, 
     if (outer >= kMaxRefine || !(rr < 0.25 * rr_prev) || total >= maxit) {
       // hand over to the float64 kernel from the current iterate
       p->mixed_handovers += 1;
-      CUCHK(p, pcg_launch(pcg_args(p, side, b, x, std::max(1, maxit - total), tol, false), side, st));
+      TRY(run_pcg(p, side, b, x, std::max(1, maxit - total), tol, false));
       TRY(readback(p, 0, 1, true));
       hs = p->hs->stat[side];
       hs.iters += total;
@@ -672,7 +718,7 @@ cr_status launch_pcg_mixed(cr_problem* p, int side, const double* b, double* x, 
     }
     rr_prev = rr;
     fill(n, 0.0, d, st);
-    CUCHK(p, pcg_launch(pcg_args(p, side, r, d, maxit - total, kMixedInnerTol, true), side, st));
+    TRY(run_pcg(p, side, r, d, maxit - total, kMixedInnerTol, true));
     TRY(readback(p, 0, 1, true));
     const PcgStat in = p->hs->stat[side];
     total += in.iters;

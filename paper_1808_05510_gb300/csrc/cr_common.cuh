@@ -97,6 +97,19 @@ struct PcgArgs {
   int fp32;                // 1: float32 vectors and arithmetic, float64 inner products and scalars
 };
 
+// ---------------------------------------------------------------- cr_pcg_grid.cu
+// Grid-wide PCG (vectors in HBM, all SMs) for grids beyond one cluster.
+// Blocks of the cooperative launch (0: cannot run) and work doubles needed.
+int pcg_grid_blocks(bool fp32, int m, int K);
+size_t pcg_grid_work_elems(int n);
+// Solves the system of `a` (side 0: Eq. ALS_linsys, 1: Eq. ALS_linsys_v) with
+// a.dinv, a.omt precomputed in float64 (fcg_jacobi_diag).  work: 9n doubles;
+// part: nb*4, ypart: nb*m, yglob: m doubles; bar: 2 unsigned; err: 1 int.
+// a.stat receives iterations and status (3 = grid barrier timed out).
+cudaError_t pcg_grid_launch(const PcgArgs& a, int side, const int* xc_ptr, const int* xc_row, const double* xc_val,
+                            double* work, double* part, double* ypart, double* yglob, unsigned* bar, int* err,
+                            int nb, cudaStream_t st);
+
 // ---------------------------------------------------------------- cr_pcg.cu
 cudaError_t pcg_launch(const PcgArgs& a, int data_kind, cudaStream_t st);
 cudaError_t pcg_prepare(int data_kind, int csize, size_t smem_bytes);

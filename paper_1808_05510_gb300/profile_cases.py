@@ -7,6 +7,11 @@
         two Galerkin projections (Eq. Proj_Sylv) at rank 60 from a float64 greedy run
     python -m paper_1808_05510_gb300.profile_cases assembly tc
         three tensor-core assemblies of G_a = U^T diag(Omega_a) U at rank 100
+    python -m paper_1808_05510_gb300.profile_cases pcg_stress fp32|fp64 [solves]
+        u-side ALS solves on the ~4M-voxel stress shell (grid-wide PCG, vectors in
+        HBM): fp32 = one float32 grid solve to 1e-5 inside the mixed form's
+        refinement, fp64 = float64 grid solve to 1e-5; prints iterations and the
+        CUDA-event time of each solve
 """
 from __future__ import annotations
 
@@ -64,6 +69,37 @@ def assembly(form: str) -> None:
         print("assembled", G.shape, flush=True)
 
 
+def pcg_stress(form: str, solves: int = 2) -> None:
+    import torch
+
+    from . import synth
+    from .conreg import CR_FP64, CR_MIXED, ConReg
+
+    p = synth.stress_shell()
+    v = p.X.sum(axis=1)
+    v /= np.linalg.norm(v)
+    rhs = np.random.default_rng(3).standard_normal(p.ny)
+    prec = CR_MIXED if form == "fp32" else CR_FP64
+    # mixed: outer tolerance at the inner one, so each solve is one float32 grid launch
+    with ConReg.from_problem(p, r_cap=2, precision=prec, pcg_tol=1e-5, pcg_maxit=200000, profile=1) as g:
+        for _ in range(solves):
+            g.cr_get_stats(reset=True)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(g.stream)
+            _, it = g.cr_solve_u(v, rhs)
+            e1.record(g.stream)
+            e1.synchronize()
+            st = g.cr_get_stats()
+            kms, kn = st["phase_ms"]["pcg_kernel"], st["phase_calls"]["pcg_kernel"]
+            print(f"voxels {p.ny} iterations {it} solve_ms {e0.elapsed_time(e1):.3f} "
+                  f"pcg_phase_ms {st['phase_ms']['pcg_u']:.3f} kernel_ms {kms:.3f} launches {kn} "
+                  f"kernel_us_per_iter {1e3 * kms / max(it, 1):.1f}", flush=True)
+
+
 if __name__ == "__main__":
     case, form = sys.argv[1], (sys.argv[2] if len(sys.argv) > 2 else "fp64")
-    {"pcg": pcg, "galerkin": galerkin, "assembly": assembly}[case](form)
+    if case == "pcg_stress":
+        pcg_stress(form, int(sys.argv[3]) if len(sys.argv) > 3 else 2)
+    else:
+        {"pcg": pcg, "galerkin": galerkin, "assembly": assembly}[case](form)

@@ -125,19 +125,17 @@ def grid_laplacian(grid: Grid) -> CSR:
             nbrs.append(j)
     nbrs = np.stack(nbrs, axis=1)  # (n, 2d)
     deg = (nbrs >= 0).sum(axis=1)
-    # entries (i, i, deg_i) and (i, j, -1) for every face neighbour j, sorted by (row, column)
-    ri = np.repeat(np.arange(n), nbrs.shape[1])
-    cj = nbrs.ravel()
-    keep = cj >= 0
-    rows = np.concatenate([np.arange(n), ri[keep]])
-    cols_ = np.concatenate([np.arange(n), cj[keep]])
-    vals = np.concatenate([deg.astype(np.float64), -np.ones(int(keep.sum()))])
-    order = np.lexsort((cols_, rows))
-    rows, cols_, vals = rows[order], cols_[order], vals[order]
-    rowptr = np.zeros(n + 1, dtype=np.int64)
-    np.add.at(rowptr, rows + 1, 1)
-    rowptr = np.cumsum(rowptr).astype(np.int32)
-    cols = cols_
+    # each row: the diagonal (i, deg_i) and (i, j, -1) for every face neighbour j,
+    # columns ascending.  Indices follow the row-major voxel order, so the face
+    # neighbours of i sort as -axis0 < ... < -axis_last < i < +axis_last < ... < +axis0.
+    d = mask.ndim
+    order = [2 * ax for ax in range(d)] + [-1] + [2 * ax + 1 for ax in reversed(range(d))]
+    ent = np.stack([np.arange(n) if k < 0 else nbrs[:, k] for k in order], axis=1)
+    keep = ent >= 0
+    cols = ent[keep]
+    rows = np.broadcast_to(np.arange(n)[:, None], ent.shape)[keep]
+    vals = np.where(cols == rows, deg[rows].astype(np.float64), -1.0)
+    rowptr = np.concatenate([[0], np.cumsum(keep.sum(axis=1))]).astype(np.int32)
     return CSR(n, rowptr, np.asarray(cols, dtype=np.int32), np.asarray(vals, dtype=np.float64))
 
 
@@ -297,6 +295,28 @@ def whole_cortex(seed: int = 1811, shape=(96, 64, 80), n_target: int = 45000, m:
     g = Grid(shell_mask(shape, n_target))
     X = gaussian_injections(g, m, rng, 2.0, 5.0, 0.2, 1.0)
     return _finish(f"cortex-{g.n}vox-m{m}", g, g, X, rng, lam, r_max, sparse_cut=1e-3)
+
+
+def stress_shell(seed: int = 1816, side: int = 256, n_target: int = 4_000_000, m: int = 8,
+                 lam: float = 1e3) -> Problem:
+    """Roofline stress shape: an ellipsoidal shell of ~4M voxels in a 256^3 box
+    (outer semi-axes 0.46 side, thickness from the shell volume
+    V (1 - (1 - t)^3) = n_target), 7-point Laplacian, m Gaussian injections,
+    Omega = 1{X <= 0.4}, Y random on Omega (only the sub-solves run on it)."""
+    rng = np.random.default_rng(seed)
+    a = 0.46 * side
+    vol = 4.0 / 3.0 * math.pi * a ** 3
+    t = 1.0 - (1.0 - min(0.999, n_target / vol)) ** (1.0 / 3.0)
+    c = (side - 1) / 2.0
+    z, y, x = np.ogrid[:side, :side, :side]
+    rho2 = ((z - c) / a) ** 2 + ((y - c) / a) ** 2 + ((x - c) / a) ** 2
+    mask = (rho2 <= 1.0) & (rho2 >= (1.0 - t) ** 2)
+    g = Grid(mask)
+    X = gaussian_injections(g, m, rng, 2.0, 3.0, 1.0, 1.0)
+    Omega = (X <= 0.4).astype(np.uint8)
+    Y = rng.standard_normal((g.n, m)) * Omega
+    L = grid_laplacian(g)
+    return Problem(f"stress-shell-{g.n}vox-m{m}", g, g, L, L, X, Y, Omega, float(lam), 2)
 
 
 def sweep_cortex(seed: int = 1814, box: int = 40, n_target: int = 15000, m: int = 126, lam: float = 1e2,

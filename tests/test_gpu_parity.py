@@ -84,7 +84,7 @@ def test_residual_products_set_state(cr, prob):
         assert np.array_equal(Ug, U) and np.array_equal(Zg, Z) and np.array_equal(Vg, V)
 
 
-@pytest.mark.parametrize("kernel", [0, 1], ids=["auto", "generic"])
+@pytest.mark.parametrize("kernel", [0, 1, 2], ids=["auto", "generic", "grid"])
 def test_als_subsolves(cr, prob, kernel):
     p, o = prob
     rng = np.random.default_rng(4)
