@@ -112,6 +112,8 @@ typedef struct {
   void* alloc_ctx;
   int32_t galerkin_ctas;   /* CTA cap of the persistent Galerkin kernel; 0 = one CTA per SM.  Problems
                               that share the GPU (cr_solve_batch) cap it so that their launches co-run. */
+  int32_t learned_judge;   /* how Jacobi-PCG judges the learned preconditioner (cr_set_preconditioner):
+                              0 = by time (default), 1 = by iterations */
 } cr_options;
 
 typedef struct {
@@ -360,11 +362,14 @@ cr_status cr_set_voxel_grid(struct cr_problem* p, int32_t side, const int32_t* d
 
 /* Attach a network (NULL detaches); its box must match the voxel grids.
  * Jacobi-PCG judges the network, per side: the first sub-solve after attaching
- * runs Jacobi-PCG and records its iteration count k_J; each later learned solve
- * may take at most 2 k_J + 16 flexible-CG iterations, after which Jacobi-PCG
- * finishes it from the current iterate (a fallback); three fallbacks in a row
- * switch the learned form off for that side until the next attach.  cr_stats
- * counts learned solves, fallbacks and the switched-off sides. */
+ * runs Jacobi-PCG and records its iteration count k_J and its time t_J.  Each
+ * later learned solve may take at most 2 k_J + 16 flexible-CG iterations and,
+ * when judging by time (cr_options.learned_judge = 0), at most 2 t_J; if it
+ * has not converged by then, Jacobi-PCG finishes it from the current iterate
+ * (a fallback).  By time, an attempt that falls back or takes longer than t_J
+ * is a loss and two losses in a row switch the learned form off for that side;
+ * by iterations, three fallbacks in a row do.  Off lasts until the next
+ * attach.  cr_stats counts learned solves, fallbacks and the switched-off sides. */
 cr_status cr_set_preconditioner(struct cr_problem* p, struct cr_net* net);
 
 /* Static description of a status code. */

@@ -50,7 +50,7 @@ class cr_options(C.Structure):
                 ("galerkin_maxit", C.c_int32), ("residual_every", C.c_int32), ("cluster_size", C.c_int32),
                 ("profile", C.c_int32), ("pcg_kernel", C.c_int32), ("galerkin_kernel", C.c_int32),
                 ("seed", C.c_uint64), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
-                ("alloc_ctx", C.c_void_p), ("galerkin_ctas", C.c_int32)]
+                ("alloc_ctx", C.c_void_p), ("galerkin_ctas", C.c_int32), ("learned_judge", C.c_int32)]
 
 
 class cr_rank1_info(C.Structure):

@@ -116,6 +116,7 @@ struct cr_problem {
   // a Jacobi-PCG solve (0 = not measured yet), consecutive fallbacks, and whether
   // the learned form has been switched off for this side
   int jac_iters[2] = {0, 0};
+  double jac_sec[2] = {0.0, 0.0};  // host time of the judge's Jacobi-PCG solve
   int learned_streak[2] = {0, 0};
   bool learned_off[2] = {false, false};
   // BF16 hi/lo shadows of U (n_y x 128, column stride ldb) for the tensor-core assembly
@@ -524,6 +525,9 @@ cr_status fcg_learned(cr_problem* p, int side, const double* b, double* x) {
   double* sc = p->ds + DS_FCG;
   double *r = p->pr, *q = p->pw, *pv = p->pp, *z = p->ps, *rold = p->fc_rold, *dd = p->fc_d, *t = p->fc_t;
   const double tol = p->opt.pcg_tol;
+  const bool by_time = p->opt.learned_judge == 0;
+  const auto t_start = std::chrono::steady_clock::now();
+  auto elapsed = [&]() { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count(); };
   prof_begin(p, side == 0 ? CR_PHASE_PCG_U : CR_PHASE_PCG_V);
   fcg_jacobi_diag(L, p->lam, coef, side, p->m, p->Om, p->ny, p->xi, p->xl, p->svec, p->pomt, p->pdinv, st);
   fcg_apply(L, p->lam, coef, side, p->pomt, p->xl, p->xc_ptr, p->xc_row, p->xc_val, p->m, p->svec, p->fc_y, x, t, q,
@@ -558,21 +562,26 @@ cr_status fcg_learned(cr_problem* p, int side, const double* b, double* x) {
       TRY(readback(p, DS_FCG, 3, false));
       rr = p->hs->ds[DS_FCG + 2];
       if (!std::isfinite(rr)) break;
+      if (by_time && elapsed() > 2.0 * p->jac_sec[side]) break;  // already twice the Jacobi solve's time
     }
   }
   prof_end(p, side == 0 ? CR_PHASE_PCG_U : CR_PHASE_PCG_V);
   PcgStat hs{k, 0, bb > 0.0 ? std::sqrt(std::max(rr, 0.0) / bb) : 0.0, std::sqrt(bb)};
-  if (bb > 0.0 && !(rr <= tol2)) {
-    // fallback: Jacobi-PCG from the current iterate; three fallbacks in a row
-    // switch the learned form off for this side
+  const bool converged = !(bb > 0.0) || rr <= tol2;
+  const bool loss = !converged || (by_time && elapsed() > p->jac_sec[side]);
+  if (loss) {
+    if (++p->learned_streak[side] >= (by_time ? 2 : 3)) p->learned_off[side] = true;
+  } else {
+    p->learned_streak[side] = 0;
+  }
+  if (!converged) {
+    // fallback: Jacobi-PCG from the current iterate
     p->fcg_fallbacks += 1;
-    if (++p->learned_streak[side] >= 3) p->learned_off[side] = true;
     TRY(launch_pcg_jacobi(p, side, b, x, p->opt.pcg_maxit));
     TRY(readback(p, 0, 1, true));
     hs = p->hs->stat[side];
     hs.iters += k;
   } else {
-    p->learned_streak[side] = 0;
     p->learned_solves += 1;
   }
   CUCHK(p, cudaMemcpyAsync(p->stat + side, &hs, sizeof(PcgStat), cudaMemcpyHostToDevice, st));
@@ -582,9 +591,12 @@ cr_status fcg_learned(cr_problem* p, int side, const double* b, double* x) {
 cr_status launch_pcg(cr_problem* p, int side, const double* b, double* x) {
   if (p->opt.precond == CR_PRECOND_LEARNED && p->net && p->box[side] && !p->learned_off[side]) {
     if (p->jac_iters[side] > 0) return fcg_learned(p, side, b, x);
-    // first solve on this side: Jacobi-PCG, whose iteration count judges the learned form
+    // first solve on this side: Jacobi-PCG, whose iterations and time judge the learned form
+    TRY(sync(p));
+    const auto t0 = std::chrono::steady_clock::now();
     TRY(launch_pcg_jacobi(p, side, b, x, p->opt.pcg_maxit));
     TRY(readback(p, 0, 1, true));
+    p->jac_sec[side] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     p->jac_iters[side] = std::max(1, p->hs->stat[side].iters);
     return CR_OK;
   }
@@ -1618,6 +1630,7 @@ cr_status cr_set_preconditioner(cr_problem* p, cr_net* net) {
   p->net = net;
   for (int s = 0; s < 2; ++s) {
     p->jac_iters[s] = p->learned_streak[s] = 0;
+    p->jac_sec[s] = 0.0;
     p->learned_off[s] = false;
   }
   return sync(p);
@@ -1640,7 +1653,9 @@ cr_status cr_galerkin_assembly(cr_problem* p, int32_t method, float* G_host, int
                                ld * sizeof(float), j * sizeof(float), j, cudaMemcpyDeviceToHost, p->st));
   p->d2h_bytes += (int64_t)sizeof(float) * p->m * j * j;
   TRY(sync(p));
-  if (herr) return fail(p, CR_ETIMEOUT, "tensor-core assembly: an mbarrier wait timed out");
+  if (herr)
+    return fail(p, CR_ETIMEOUT, "tensor-core assembly: an mbarrier wait timed out (site*100000 + K-block + 1 = " +
+                                    std::to_string(herr) + ")");
   return CR_OK;
 }
 

@@ -34,6 +34,7 @@ constexpr int kTileRows = 128;  // M = N
 constexpr int kKBlock = 64;     // voxels per K-block (128 bytes of BF16)
 constexpr int kTileBytes = kTileRows * kKBlock * 2;  // 16 KB
 constexpr uint32_t kSpinLimit = 1u << 26;
+constexpr uint64_t kWaitNs = 500000000ull;  // 0.5 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -63,7 +64,15 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
 }
 
 // Bounded wait for the phase with parity `parity` to complete; false on timeout.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// at most kSpinLimit polls and kWaitNs of wall-clock time (a poll may suspend the thread)
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const uint64_t t0 = global_ns();
   for (uint32_t spin = 0; spin < kSpinLimit; ++spin) {
     uint32_t done;
     asm volatile(
@@ -74,8 +83,14 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (done) return true;
+    if (global_ns() - t0 > kWaitNs) break;
   }
   return false;
+}
+
+// The first timeout wins: site (1 = tiles loaded, 2 = MMAs done) * 100000 + K-block + 1.
+__device__ __forceinline__ void record_timeout(int* err, int site, int kb) {
+  atomicCAS(err, 0, site * 100000 + kb + 1);
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
@@ -169,7 +184,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (i < a.n && a.Om[i + (int64_t)alpha * a.ldo] == 0) masked_block = 1;
     }
     if (!mbar_wait(bfull, phase)) {
-      atomicExch(a.err, 1);
+      record_timeout(a.err, 1, kb);
       failed = 1;
     }
     __syncthreads();
@@ -206,7 +221,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     issued = true;
     // the next TMA / masked copy overwrites the tiles: wait for these MMAs
     if (!mbar_wait(bmma, phase)) {
-      atomicExch(a.err, 1);
+      record_timeout(a.err, 2, kb);
       failed = 1;
     }
     __syncthreads();

@@ -167,11 +167,11 @@ def compare_iterations(p: Problem, net: "conreg.ConvNet", ranks: List[int], tol:
 
     The learned problem's first solve on each side is its Jacobi judge run
     (cr_set_preconditioner), so one calibration solve per side precedes the
-    measured ones."""
+    measured ones; the judge counts iterations (what the network changes)."""
     out = []
     with conreg.ConReg.from_problem(p, r_cap=max(max(ranks), 1), pcg_tol=tol, pcg_maxit=100000) as gj, \
             conreg.ConReg.from_problem(p, r_cap=max(max(ranks), 1), pcg_tol=tol, pcg_maxit=100000,
-                                       precond=conreg.CR_PRECOND_LEARNED) as gl:
+                                       precond=conreg.CR_PRECOND_LEARNED, learned_judge=1) as gl:
         gl.cr_set_voxel_grid(0, p.grid_y.mask)
         gl.cr_set_voxel_grid(1, p.grid_x.mask)
         gl.cr_set_preconditioner(net)

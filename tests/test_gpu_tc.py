@@ -29,9 +29,11 @@ def cr():
     return conreg
 
 
-@pytest.mark.parametrize("name,j", [("toy2d", 6), ("masked3d", 40), ("masked3d", 128)])
+@pytest.mark.parametrize("name,j", [("toy2d", 6), ("toy2d9", 20), ("masked3d", 40), ("masked3d", 100),
+                                    ("masked3d", 128), ("visual", 64)])
 def test_tensor_core_assembly(cr, name, j):
-    p = synth.toy2d() if name == "toy2d" else synth.masked3d()
+    p = {"toy2d": lambda: synth.toy2d(), "toy2d9": lambda: synth.toy2d(m=9),
+         "masked3d": lambda: synth.masked3d(), "visual": lambda: synth.visual_cortex()}[name]()
     o = Oracle.from_problem(p)
     rng = np.random.default_rng(40 + j)
     U, _ = np.linalg.qr(rng.standard_normal((p.ny, j)))
