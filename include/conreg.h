@@ -39,7 +39,7 @@ typedef enum {
   CR_ENOMEM = 2,    /* device allocation failed; nothing leaked */
   CR_ECUDA = 3,     /* a CUDA runtime call failed */
   CR_ENOTCONV = 4,  /* an iteration hit its cap; the best iterate is kept */
-  CR_ETIMEOUT = 5,  /* reserved: wall-clock budget exceeded */
+  CR_ETIMEOUT = 5,  /* a bounded device-side wait gave up (grid barrier, mbarrier) */
   CR_ERANK = 6,     /* orthogonalisation rejected a new column (rank deficient) */
   CR_ESTATE = 7     /* call not valid in the current state (e.g. rank capacity reached) */
 } cr_status;
@@ -99,9 +99,11 @@ typedef struct {
   int32_t residual_every;  /* cr_solve: evaluate ‖R‖_F every k steps (default 1) */
   int32_t cluster_size;    /* PCG thread-block cluster size; 0 = automatic */
   int32_t profile;         /* != 0: time each phase with CUDA events (see cr_get_stats) */
-  int32_t pcg_kernel;      /* 0 = automatic: the cluster-resident kernel (register-resident variant when it
-                              applies) while the grid fits one cluster's shared memory, else the grid-wide
-                              kernel; 1 = generic cluster kernel; 2 = always the grid-wide kernel */
+  int32_t pcg_kernel;      /* 0 = automatic: the register-resident cluster kernel (the whole solve on
+                              chip) while it applies (unit-weight Laplacian, at most 6 neighbours per
+                              row, up to 1,024 rows per CTA in float64 or 2,048 in float32), else the
+                              grid-wide kernel; 1 = the generic cluster kernel (grids that fit one
+                              cluster); 2 = always the grid-wide kernel */
   int32_t galerkin_kernel; /* 0 = one persistent cooperative launch per projection, 1 = one launch per step */
   uint64_t seed;           /* seed of the fallback ALS start vector */
   void* stream;            /* cudaStream_t for all device work; NULL = a library-owned stream */
@@ -250,8 +252,8 @@ cr_status cr_get_stats(struct cr_problem* p, cr_stats* s, int32_t reset);
  * a packaging of the library's u-side PCG for such callers.
  *
  * Solves (lambda [(L + c I)^2 + (d - c^2) I] + diag(omega)) u_hat = rhs from
- * u_hat = 0 by the same cluster-resident Jacobi PCG as cr_solve_u, to relative
- * residual tol or maxit iterations.  L (n x n) is given in CSR form in device
+ * u_hat = 0 by a cluster-resident Jacobi PCG (the algorithm of cr_solve_u's
+ * cluster kernels), to relative residual tol or maxit iterations.  L (n x n) is given in CSR form in device
  * memory (int32 rowptr[n+1], col[nnz], float64 val[nnz]); omega, rhs and u_hat
  * are device vectors of n entries; stream is a cudaStream_t (NULL = default).
  * *iters (host, may be NULL) receives the iteration count.

@@ -114,6 +114,8 @@ cudaError_t pcg_grid_launch(const PcgArgs& a, int side, const int* xc_ptr, const
 cudaError_t pcg_launch(const PcgArgs& a, int data_kind, cudaStream_t st);
 cudaError_t pcg_prepare(int data_kind, int csize, size_t smem_bytes);
 size_t pcg_smem_bytes(int chunk, int m);
+// rows per thread of the register-resident cluster kernel for this operator, 0 if it does not apply
+int pcg_reg_vpt(const DevLap& L, bool fp32);
 bool pcg_cluster_ok(int csize, size_t smem_bytes);
 // y = (L + shift I) x
 void lap_apply(const DevLap& L, const double* x, double* y, double shift, cudaStream_t st);
