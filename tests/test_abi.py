@@ -94,3 +94,37 @@ def test_create_rejects_invalid_input(lib, case):
 
 def test_destroy_null_is_noop(lib):
     lib.cr_destroy(None)
+
+
+STRUCTS = ["cr_csr", "cr_problem_desc", "cr_options", "cr_rank1_info", "cr_proj_info", "cr_stats", "cr_solve_info",
+           "cr_member", "cr_member_result"]
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets
+    that a C compiler gives the header's struct (binding drift would silently
+    garble the fields after the first mismatch)."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "conreg.h"', "int main(void) {"]
+    for name in STRUCTS:
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for field, _ in getattr(cr, name)._fields_:
+            cfield = field.rstrip("_")
+            lines.append(f'  printf("{name}.{field} %zu\\n", offsetof({name}, {cfield}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.dirname(HDR), str(src), "-o", str(exe)], check=True)
+    out = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    for name in STRUCTS:
+        st = getattr(cr, name)
+        assert int(out[name]) == C.sizeof(st), name
+        for field, _ in st._fields_:
+            assert int(out[f"{name}.{field}"]) == getattr(st, field).offset, f"{name}.{field}"
