@@ -35,6 +35,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_1808_05510_gb300 import replicas  # noqa: E402  (host-side cross-rank scalars only)
+
 METRIC = "time-to-rel-residual 1e-6 and rank-1 updates/s, mixed/learned vs plain FP64 GPU"
 UNIT = "rank-1 updates/s"
 
@@ -270,15 +272,11 @@ def run_ours(args, rank, world, local_rank):
         g.close()
         tot_ms = sum(ms)
         ranks = sum(i["rank"] for i in infos)
-        t_local = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
-        r_local = torch.tensor([float(ranks)], dtype=torch.float64, device=dev)
         if world > 1:
             import torch.distributed as dist
             dist.barrier()
-            dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-            dist.all_reduce(r_local, op=dist.ReduceOp.SUM)
-        t_max = float(t_local.item())
-        value = float(r_local.item()) / (t_max / 1e3)
+        all_ranks, t_max = replicas.aggregate(ranks, tot_ms, world, dev)
+        value = all_ranks / (t_max / 1e3)
         reached = [i for i in infos if i["stop_name"] == "relres"]
         ttr = (sum(m for m, i in zip(ms, infos) if i["stop_name"] == "relres") / len(reached) / 1e3) if reached else None
         # the PCG kernel's own launches (CUDA events around each launch, on the
@@ -325,7 +323,7 @@ def run_ours(args, rank, world, local_rank):
         forms["learned"] = lf
         net.close()
     if not args.no_batch:
-        forms["batched"] = measure_batch(args)
+        forms["batched"] = measure_batch(args, rank, world, dev)
     ttr_toy = None if args.no_ttr else measure_ttr_toy(args)
     head = forms[args.precision]
     hbm, peak_kind = peaks()
@@ -364,15 +362,10 @@ def run_ours(args, rank, world, local_rank):
             e_ms.append(el)
             e_ranks += info["rank"]
             h2d, d2h = st["h2d_bytes"], st["d2h_bytes"]
-        e_t = torch.tensor([sum(e_ms)], dtype=torch.float64, device=dev)
-        e_r = torch.tensor([float(e_ranks)], dtype=torch.float64, device=dev)
-        if world > 1:
-            import torch.distributed as dist
-            dist.all_reduce(e_t, op=dist.ReduceOp.MAX)
-            dist.all_reduce(e_r, op=dist.ReduceOp.SUM)
-        out["e2e"] = {"value": float(e_r.item()) / (float(e_t.item()) / 1e3), "unit": UNIT,
+        e_r, e_t = replicas.aggregate(e_ranks, sum(e_ms), world, dev)
+        out["e2e"] = {"value": e_r / (e_t / 1e3), "unit": UNIT,
                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                      "ms_per_step": float(e_t.item()) / args.steps}
+                      "ms_per_step": e_t / args.steps}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = oracle_sample(p, args, args.cpu_seconds)
     if rank == 0:
@@ -412,12 +405,14 @@ def measure_ttr_toy(args, runs: int = 3):
     return out
 
 
-def measure_batch(args):
+def measure_batch(args, rank=0, world=1, dev="cuda"):
     """Batched form: the lambda x fold sweep (16 lambdas log-spaced 1..1e6 x 5 folds
     of a 126-injection, ~15,000-voxel data set; every member fits 96-106
     injections) in the mixed form, after the autotuner picked its launch shape.
     Beside it, one member at a time (concurrency 1) on a 16-member sample, one
-    member per lambda, to show what running members side by side gains."""
+    member per lambda, to show what running members side by side gains.  With
+    several ranks every rank solves its shard of the members (weak in GPUs,
+    strong in members) and the per-member scores are gathered on the host."""
     import torch
     from paper_1808_05510_gb300 import sweep, synth as _synth
     from paper_1808_05510_gb300.conreg import CR_MIXED, solve_batch
@@ -425,7 +420,8 @@ def measure_batch(args):
     t0 = time.perf_counter()
     bp = _synth.sweep_cortex()
     folds = _synth.fold_partition(bp.m)
-    mem = _synth.sweep_members(bp.m, _synth.lambda_grid(), folds)
+    mem_all = _synth.sweep_members(bp.m, _synth.lambda_grid(), folds)
+    mem = replicas.shard_members(mem_all, rank, world)
     gen_s = time.perf_counter() - t0
     solve_batch(bp, mem[:9], r_max=2, tau=args.tau, precision=CR_MIXED)  # warm-up
     shape = sweep.autotune(bp, mem, r_probe=2, tau=args.tau, precision=CR_MIXED)
@@ -433,22 +429,27 @@ def measure_batch(args):
         res, sec = sweep._timed_batch(bp, mem, args.batch_r, tau=args.tau, relres_target=args.relres,
                                       concurrency=shape["concurrency"], cluster_size=shape["cluster_size"],
                                       precision=CR_MIXED)
-    ranks = sum(r["rank"] for r in res)
-    sample = mem[::5]
+    ranks, ms_max = replicas.aggregate(sum(r["rank"] for r in res), 1e3 * sec, world, dev)
+    sec = ms_max / 1e3
+    sample = mem[::max(1, 5 // world)]
     seq, seq_sec = sweep._timed_batch(bp, sample, args.batch_r, tau=args.tau, relres_target=args.relres,
                                       concurrency=1, precision=CR_MIXED)
-    seq_ranks = sum(r["rank"] for r in seq)
-    cv = sweep.cv_summary(mem, res)
+    seq_ranks, seq_ms = replicas.aggregate(sum(r["rank"] for r in seq), 1e3 * seq_sec, world, dev)
+    seq_sec = seq_ms / 1e3
+    # per-member scores of every rank, for the cross-validation curve
+    scored = [(m, r) for part in replicas.gather_objects(list(zip(mem, res)), world) for m, r in part]
+    cv = sweep.cv_summary([m for m, _ in scored], [r for _, r in scored])
+    res = [r for _, r in scored]
     status = {}
     for r in res:
         status[str(r["status"])] = status.get(str(r["status"]), 0) + 1
     torch.cuda.synchronize()
     return {"value": ranks / sec, "unit": UNIT + " (aggregate over members)", "seconds": sec,
-            "members": len(mem), "voxels": bp.nx, "ninj_total": bp.m,
+            "members": len(mem_all), "members_per_rank": len(mem), "voxels": bp.nx, "ninj_total": bp.m,
             "ninj_fit": sorted({len(f) for _, f, _ in mem}), "r_max": args.batch_r, "precision": "mixed",
             "ranks": ranks, "shape": {k: shape[k] for k in ("concurrency", "cluster_size")},
             "autotune": shape["table"], "status_counts": status,
-            "sequential_sample": {"members": len(sample), "seconds": seq_sec, "value": seq_ranks / seq_sec},
+            "sequential_sample": {"members": len(sample) * world, "seconds": seq_sec, "value": seq_ranks / seq_sec},
             "speedup_vs_sequential": (ranks / sec) / (seq_ranks / seq_sec),
             "pcg_iters": sum(r["pcg_iters"] for r in res), "galerkin_cg_iters": sum(r["cg_iters"] for r in res),
             "best_lambda": cv["best_lambda"], "cv_by_lambda": {f"{k:.3g}": v for k, v in cv["cv_by_lambda"].items()},
