@@ -108,7 +108,7 @@ struct cr_problem {
   double *cv_X = nullptr, *cv_Y = nullptr, *cv_T1 = nullptr, *cv_T2 = nullptr, *cv_P = nullptr, *cv_out = nullptr;
   uint8_t* cv_Om = nullptr;
   int64_t fcg_fallbacks = 0, learned_solves = 0, mixed_handovers = 0;
-  // grid-wide PCG (grids beyond one cluster, or pcg_kernel = 2): work buffers
+  // grid-wide PCG (grids the register-resident kernel does not take, or pcg_kernel = 2): work buffers
   double *pg_work = nullptr, *pg_part = nullptr, *pg_ypart = nullptr, *pg_yglob = nullptr;
   unsigned* pg_bar = nullptr;
   int* pg_err = nullptr;
@@ -648,8 +648,8 @@ bool use_grid_pcg(const cr_problem* p, int side, bool fp32) {
 }
 
 // One Jacobi-PCG solve on the cluster-resident kernel, or on the grid-wide
-// kernel for grids beyond one cluster (that path waits for the result, to
-// turn a grid barrier timeout into CR_ETIMEOUT).
+// kernel (use_grid_pcg; that path waits for the result, to turn a grid
+// barrier timeout into CR_ETIMEOUT).
 cr_status run_pcg(cr_problem* p, int side, const double* b, double* x, int maxit, double tol, bool fp32) {
   if (!use_grid_pcg(p, side, fp32)) {
     prof_begin(p, CR_PHASE_PCG_KERNEL);

@@ -98,7 +98,7 @@ struct PcgArgs {
 };
 
 // ---------------------------------------------------------------- cr_pcg_grid.cu
-// Grid-wide PCG (vectors in HBM, all SMs) for grids beyond one cluster.
+// Grid-wide PCG (vectors in HBM, all SMs) for grids the register-resident cluster kernel does not take.
 // Blocks of the cooperative launch (0: cannot run) and work doubles needed.
 int pcg_grid_blocks(bool fp32, int m, int K);
 size_t pcg_grid_work_elems(int n);

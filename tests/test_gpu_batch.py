@@ -75,7 +75,8 @@ def test_batch_concurrency_does_not_change_results(cr, data):
 def test_batch_mixed_form_close_to_fp64(cr, data):
     """The sweep in the mixed form (float32 sub-solves and inner Galerkin CG,
     float64 refinement): relative residual and held-out error within 1e-4 of
-    the float64 sweep (the float32 PCG tolerance 1e-6 bounds each ALS step)."""
+    the float64 sweep (sub-solves and Galerkin solves are refined to the float64
+    tolerances; what remains is float32 rounding in the inner solves)."""
     p, members = data
     f64 = cr.solve_batch(p, members, r_max=R, tau=1e-12, concurrency=4)
     mix = cr.solve_batch(p, members, r_max=R, tau=1e-12, concurrency=4, precision=cr.CR_MIXED)
