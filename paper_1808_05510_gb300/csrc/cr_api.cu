@@ -418,12 +418,19 @@ void sym_eig(int n, std::vector<double> A, std::vector<double>& w, std::vector<d
         tot += x * x;
         if (a != b) off += x * x;
       }
-    if (off <= 1e-32 * tot || off == 0.0) break;
+    // converged once the off-diagonal mass is at the rounding level of the matrix
+    constexpr double eps = 2.220446049250313e-16;
+    if (off <= (double)n * n * eps * eps * tot || off == 0.0) break;
     for (int pp = 0; pp < n - 1; ++pp)
       for (int qq = pp + 1; qq < n; ++qq) {
         const double apq = A[pp + (size_t)qq * n];
         if (apq == 0.0) continue;
         const double app = A[pp + (size_t)pp * n], aqq = A[qq + (size_t)qq * n];
+        if (std::fabs(apq) <= eps * std::sqrt(std::fabs(app) * std::fabs(aqq))) {
+          // negligible against its diagonal pair: no rotation needed
+          A[pp + (size_t)qq * n] = A[qq + (size_t)pp * n] = 0.0;
+          continue;
+        }
         const double th = (aqq - app) / (2.0 * apq);
         const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
         const double cth = 1.0 / std::sqrt(t * t + 1.0), sth = t * cth;
