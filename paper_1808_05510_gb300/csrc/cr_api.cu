@@ -521,9 +521,11 @@ cr_status launch_pcg_jacobi(cr_problem* p, int side, const double* b, double* x,
 cr_status launch_pcg_mixed(cr_problem* p, int side, const double* b, double* x, int maxit);
 
 // Flexible CG (Polak-Ribiere) with the learned preconditioner
-// z = D^-1 r + s net(D^-1 r / s, mask); float64 vectors.  If it has not
-// converged after pcg_maxit / 2 iterations the cluster Jacobi-PCG continues
-// from its iterate (fallback).  Writes the PcgStat of `side` like the PCG.
+// z = D^-1 r + s net(D^-1 r / s, mask); float64 vectors.  It may take at most
+// 2 k_J + 16 iterations and (judging by time) 2 t_J, k_J and t_J being the
+// judge's Jacobi-PCG solve on this side; if it has not converged by then,
+// Jacobi-PCG continues from its iterate (fallback).  Writes the PcgStat of
+// `side` like the PCG.
 cr_status fcg_learned(cr_problem* p, int side, const double* b, double* x) {
   cudaStream_t st = p->st;
   const DevLap& L = side == 0 ? p->Ly : p->Lx;
