@@ -409,8 +409,8 @@ def measure_batch(args, rank=0, world=1, dev="cuda"):
     """Batched form: the lambda x fold sweep (16 lambdas log-spaced 1..1e6 x 5 folds
     of a 126-injection, ~15,000-voxel data set; every member fits 96-106
     injections) in the mixed form, after the autotuner picked its launch shape.
-    Beside it, one member at a time (concurrency 1) on a 16-member sample, one
-    member per lambda, to show what running members side by side gains.  With
+    Beside it, one member at a time (concurrency 1) on an 8-member sample, every
+    other lambda, to show what running members side by side gains.  With
     several ranks every rank solves its shard of the members (weak in GPUs,
     strong in members) and the per-member scores are gathered on the host."""
     import torch
@@ -431,7 +431,7 @@ def measure_batch(args, rank=0, world=1, dev="cuda"):
                                       precision=CR_MIXED)
     ranks, ms_max = replicas.aggregate(sum(r["rank"] for r in res), 1e3 * sec, world, dev)
     sec = ms_max / 1e3
-    sample = mem[::max(1, 5 // world)]
+    sample = mem[::max(1, 10 // world)]  # 8 members, every other lambda (fold 0)
     seq, seq_sec = sweep._timed_batch(bp, sample, args.batch_r, tau=args.tau, relres_target=args.relres,
                                       concurrency=1, precision=CR_MIXED)
     seq_ranks, seq_ms = replicas.aggregate(sum(r["rank"] for r in seq), 1e3 * seq_sec, world, dev)
