@@ -20,8 +20,10 @@ import numpy as np
 
 from . import conreg
 
+# (concurrency, cluster_size): 16-CTA clusters won every probe so far, so the
+# 8-CTA shape keeps two candidates and the search spends its time on concurrency
 DEFAULT_CANDIDATES: Tuple[Tuple[int, int], ...] = tuple(
-    itertools.product((6, 9, 12, 18), (8, 16)))  # (concurrency, cluster_size)
+    itertools.product((9, 18, 27, 36), (16,))) + ((18, 8), (36, 8))
 
 
 def _timed_batch(p, members, r_max, **kw):
