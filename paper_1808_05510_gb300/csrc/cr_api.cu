@@ -910,9 +910,11 @@ cr_status do_project(cr_problem* p, double tol, cr_proj_info* info) {
   cr_status rc = CR_OK;
   if (p->opt.precision == CR_MIXED && p->gal_nb > 0) {
     // Mixed form: float64 iterative refinement.  Each outer step forms the
-    // float64 residual R = F - K(Z) and solves K dZ = R to 1e-4 relative with
-    // the persistent CG in float32 (float32 copies of the projected matrices),
-    // then Z += dZ; the stopping test is on the float64 residual.
+    // float64 residual R = F - K(Z) and solves K dZ = R to about 3e-4 relative
+    // (|r|^2 <= 1e-7 |R|^2) with the persistent CG in float32 (float32 copies of
+    // the projected matrices), then Z += dZ; the stopping test is on the float64
+    // residual.  Tighter inner solves cost more CG iterations than the outer
+    // steps they save, looser ones need more outer steps: 1e-7 measured fastest.
     mat_dot(j, j, p->F, ld, p->F, ld, gs + 3, st);
     TRY(readback(p, DS_GS + 3, 1, false));
     fn2 = p->hs->ds[DS_GS + 3];
@@ -940,12 +942,12 @@ cr_status do_project(cr_problem* p, double tol, cr_proj_info* info) {
       CUCHK(p, cudaMemsetAsync(p->gbar, 0, 2 * sizeof(unsigned), st));
       CUCHK(p, cudaMemsetAsync(p->gerr, 0, sizeof(int), st));
       cudaError_t ce = galerkin_cluster_f32_launch(j, p->m, ld, p->lam, p->fA1, p->fA2, p->fB1, p->fB2, p->fG,
-                                                   p->fH, p->fF, p->fDg, p->fZ, 1e-8 * rr, maxit, p->gout, st);
+                                                   p->fH, p->fF, p->fDg, p->fZ, 1e-7 * rr, maxit, p->gout, st);
       if (ce == cudaErrorNotSupported) {
         cudaGetLastError();
         ce = galerkin_cg_launch<float>(p->gal_nb, j, p->m, ld, p->lam, p->fA1, p->fA2, p->fB1, p->fB2, p->fG, p->fH,
                                        p->fF, p->fDg, p->fZ, p->fR, p->fPa, p->fPb, p->fQ, p->fT2, p->fT1, p->fTH,
-                                       p->fGw, p->fzb, p->gpart, p->gbar, p->gerr, 1e-8 * rr, maxit, p->gout, st);
+                                       p->fGw, p->fzb, p->gpart, p->gbar, p->gerr, 1e-7 * rr, maxit, p->gout, st);
       }
       CUCHK(p, ce);
       double out[3] = {0, 0, 0};
