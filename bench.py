@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-ttr", action="store_true")
+    ap.add_argument("--no-post", action="store_true", help="skip the post-processing measurement")
     ap.add_argument("--batch-r", type=int, default=8, help="rank of every sweep member in the batched form")
     ap.add_argument("--learn-steps", type=int, default=200)
     return ap.parse_args()
@@ -325,6 +326,7 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_batch:
         forms["batched"] = measure_batch(args, rank, world, dev)
     ttr_toy = None if args.no_ttr else measure_ttr_toy(args)
+    post = None if args.no_post else measure_post(p, args, CR_MIXED if args.precision == "mixed" else CR_FP64)
     head = forms[args.precision]
     hbm, peak_kind = peaks()
     roofline = {"bound": "hbm", "achieved": head["pcg"]["achieved"], "peak": hbm, "unit": "GB/s",
@@ -340,7 +342,7 @@ def run_ours(args, rank, world, local_rank):
            "config": cfg, "time_to_relres_s": head["time_to_relres_s"], "final_relres": head["final_relres"],
            "final_rank": head["final_rank"], "stop": head["stop"],
            "speedup_vs_fp64": head["value"] / forms["fp64"]["value"],
-           "time_to_relres_toy": ttr_toy,
+           "time_to_relres_toy": ttr_toy, "postprocess": post,
            "roofline": roofline, "gpu_launches": head["gpu_launches"], "clocks": head["clocks"],
            "forms": {k: {kk: vv for kk, vv in v.items() if kk not in ("clocks",)} for k, v in forms.items()}}
     prec_e2e = CR_MIXED if args.precision == "mixed" else CR_FP64
@@ -370,6 +372,52 @@ def run_ours(args, rank, world, local_rank):
         out["cpu_baseline"] = oracle_sample(p, args, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+# float64 FMA throughput of GB300 from its unit counts: 152 SMs x 2 FMA per SM
+# per clock x 2 flops x 2.07 GHz (the nominal 1.25 TFLOP/s)
+FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def measure_post(p, args, prec, reps: int = 5):
+    """Post-processing of the headline solution at rank r_max: the tiled pass over
+    W = U Z V^T with the nonnegative projection (statistics only, W stays on the
+    device) and the SVD of the solution, each timed with CUDA events on the
+    problem's stream (median of ``reps`` calls after one warm-up)."""
+    import torch
+
+    from paper_1808_05510_gb300.conreg import ConReg
+
+    with ConReg.from_problem(p, r_cap=args.r_max, precision=prec) as g:
+        g.cr_solve(args.r_max, args.tau, 0.0)
+        j = g.cr_get_rank()
+
+        def timed(fn):
+            ms = []
+            for k in range(reps + 1):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(g.stream)
+                res = fn()
+                e1.record(g.stream)
+                e1.synchronize()
+                if k:
+                    ms.append(e0.elapsed_time(e1))
+            return sorted(ms)[len(ms) // 2], res
+
+        rep_ms, rep = timed(lambda: g.cr_solution_report(nonneg=True))
+        svd_ms, _ = timed(lambda: g.cr_svd_factors())
+    entries = p.ny * p.nx
+    flops = 2.0 * entries * j
+    achieved = flops / (rep_ms / 1e3) / 1e12
+    return {"rank": j, "entries": entries, "report_ms": rep_ms, "svd_ms": svd_ms,
+            "entries_per_s": entries / (rep_ms / 1e3), "negative_entries": rep["n_negative"],
+            "negative_mass_rms": (rep["neg_fro2"] / entries) ** 0.5,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_TFLOPS, "kernel": "post_tile_kernel (float64 W = U Z V^T tiles)",
+                         "peak_kind": "of derived (152 SMs x 2 FP64 FMA/clk x 2.07 GHz)",
+                         "flops_per_call": flops}}
 
 
 def measure_ttr_toy(args, runs: int = 3):

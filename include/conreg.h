@@ -282,6 +282,51 @@ cr_status cr_solve_u_noalloc(int64_t n, const int32_t* rowptr_dev, const int32_t
 cr_status cr_cv_error(struct cr_problem* p, int32_t mt, const double* Xt_host, int64_t ldx, const double* Yt_host,
                       int64_t ldy, const uint8_t* Omega_t_host, int64_t ldo, double* num, double* den);
 
+/* ---- post-processing of the solution -------------------------------------- */
+
+/* Sec. 4 (leading singular vectors of the solution): W = U Z V^T is not an SVD
+ * because Z is not diagonal.  With the SVD of the core, Z = U~ S V~^T, the
+ * factors U^ = U U~ (ny x j) and V^ = V V~ (nx x j) give W = U^ S V^^T.  The
+ * j x j SVD runs on the host (one-sided Jacobi: Hestenes' method, accurate in
+ * the relative sense of Demmel and Veselic); the n x j products run on the
+ * device.  sigma receives the j singular values in descending order; U^ and
+ * V^ go to caller host buffers (leading dimensions ldu >= ny, ldv >= nx).  Any
+ * output may be NULL.  At rank 0 nothing is written.  Each singular pair is
+ * unique up to a common sign when its singular value is simple. */
+cr_status cr_svd_factors(struct cr_problem* p, double* Uhat_host, int64_t ldu, double* sigma_host,
+                         double* Vhat_host, int64_t ldv);
+
+/* Statistics of one pass over W = U Z V^T.  P(W) = max(0, W) entrywise (the
+ * projection onto the nonnegative orthant, Sec. 4) when the pass is asked to
+ * project, else W; W* is the reference solution of the pass (0 without one). */
+typedef struct {
+  int64_t entries;       /* ny * nx */
+  int64_t n_negative;    /* entries of W below zero */
+  double w_min, w_max;   /* smallest and largest entry of W */
+  double w_fro2;         /* |W|_F^2 */
+  double neg_fro2;       /* |W - max(0, W)|_F^2: squared distance of W to the nonnegative orthant */
+  double ref_fro2;       /* |W*|_F^2 */
+  double diff_fro2;      /* |P(W) - W*|_F^2 */
+  double diff_maxabs;    /* max |P(W) - W*| over the entries */
+  double rms;            /* Sec. 3: E(P(W), W*) = sqrt(diff_fro2 / (ny nx)) */
+  double rel;            /* Sec. 3: E_rel(P(W), W*) = sqrt(diff_fro2 / ref_fro2); NaN when W* = 0 */
+} cr_solution_stats;
+
+/* One tiled float64 pass over W = U Z V^T (64 x 64 tiles formed on the device;
+ * the whole ny x nx matrix is never held there).  nonneg != 0 projects each
+ * entry onto the nonnegative orthant before it is compared or returned.  The
+ * reference W* = U* Z* V*^T has rank j_ref >= 0 (0: W* = 0) and is given by
+ * caller host factors: U* (ny x j_ref, ld ldur >= ny), Z* (j_ref x j_ref,
+ * ld ldzr >= j_ref), V* (nx x j_ref, ld ldvr >= nx); they need not be
+ * orthonormal (another rank of the same problem, a truth of low rank, ...).
+ * W_host (may be NULL) receives P(W), ny x nx with ld ldw >= ny; the copy goes
+ * through a device buffer of at most 256 MiB, a block of columns at a time.
+ * Sums and extremes are reduced in a fixed order: repeated calls agree bit
+ * for bit.  Synchronises the problem's stream. */
+cr_status cr_solution_report(struct cr_problem* p, int32_t nonneg, int32_t j_ref, const double* Uref_host,
+                             int64_t ldur, const double* Zref_host, int64_t ldzr, const double* Vref_host,
+                             int64_t ldvr, double* W_host, int64_t ldw, cr_solution_stats* stats);
+
 /* ---- batched lambda x fold sweep -------------------------------------------
  * Independent greedy solves (Algorithm 1) of sub-problems of one data set: a
  * member fits the injections fit_cols (columns of X, Y, Omega) with its own

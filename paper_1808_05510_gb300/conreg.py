@@ -89,6 +89,12 @@ class cr_member_result(C.Structure):
                 ("cv_den", C.c_double), ("pcg_iters", C.c_int64), ("cg_iters", C.c_int64), ("seconds", C.c_double)]
 
 
+class cr_solution_stats(C.Structure):
+    _fields_ = [("entries", C.c_int64), ("n_negative", C.c_int64), ("w_min", C.c_double), ("w_max", C.c_double),
+                ("w_fro2", C.c_double), ("neg_fro2", C.c_double), ("ref_fro2", C.c_double),
+                ("diff_fro2", C.c_double), ("diff_maxabs", C.c_double), ("rms", C.c_double), ("rel", C.c_double)]
+
+
 # Every exported symbol with its (restype, argtypes); include/conreg.h declares the same set.
 SIGNATURES = {
     "cr_options_default": (C.c_int, [C.POINTER(cr_options)]),
@@ -124,6 +130,9 @@ SIGNATURES = {
                                      C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int32, _ip,
                                      C.c_void_p]),
     "cr_cv_error": (C.c_int, [C.c_void_p, C.c_int32, _dp, C.c_int64, _dp, C.c_int64, _up, C.c_int64, _dp, _dp]),
+    "cr_svd_factors": (C.c_int, [C.c_void_p, _dp, C.c_int64, _dp, _dp, C.c_int64]),
+    "cr_solution_report": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, _dp, C.c_int64, _dp, C.c_int64, _dp, C.c_int64,
+                                     _dp, C.c_int64, C.POINTER(cr_solution_stats)]),
     "cr_solve_batch": (C.c_int, [C.POINTER(cr_problem_desc), C.POINTER(cr_options), C.POINTER(cr_member), C.c_int32,
                                  C.c_int32, C.c_double, C.c_double, C.c_int32, C.POINTER(cr_member_result),
                                  C.POINTER(C.c_void_p)]),
@@ -328,6 +337,39 @@ class ConReg:
                                      _ptr(Omt, _up), max(1, self.ny), C.byref(num), C.byref(den)), self.h,
                "cr_cv_error")
         return num.value, den.value
+
+    def cr_svd_factors(self):
+        """(U^, sigma, V^): the SVD W = U^ diag(sigma) V^^T of the current solution (Sec. 4)."""
+        j = self.cr_get_rank()
+        Uh = np.zeros((self.ny, j), order="F")
+        Vh = np.zeros((self.nx, j), order="F")
+        s = np.zeros(j)
+        if j:
+            _check(self._lib.cr_svd_factors(self.h, _ptr(Uh), self.ny, _ptr(s), _ptr(Vh), self.nx), self.h,
+                   "cr_svd_factors")
+        return Uh, s, Vh
+
+    def cr_solution_report(self, nonneg: bool = False, ref=None, want_w: bool = False) -> dict:
+        """Statistics of W = U Z V^T (projected onto W >= 0 if ``nonneg``) against the
+        reference ``ref`` = (U*, Z*, V*) (None: W* = 0), as a dict with the fields of
+        cr_solution_stats; with ``want_w`` also "W_out" = P(W) (ny x nx)."""
+        st = cr_solution_stats()
+        jr = 0
+        Ur = Zr = Vr = None
+        if ref is not None:
+            Ur, Zr, Vr = (_f64(a) for a in ref)
+            jr = Zr.shape[0]
+        W = np.zeros((self.ny, self.nx), order="F") if want_w else None
+        nul = C.cast(None, _dp)
+        _check(self._lib.cr_solution_report(
+            self.h, 1 if nonneg else 0, jr,
+            _ptr(Ur) if jr else nul, max(1, self.ny), _ptr(Zr) if jr else nul, max(1, jr),
+            _ptr(Vr) if jr else nul, max(1, self.nx),
+            _ptr(W) if want_w else nul, max(1, self.ny), C.byref(st)), self.h, "cr_solution_report")
+        out = {k: getattr(st, k) for k, _ in cr_solution_stats._fields_}
+        if want_w:
+            out["W_out"] = W
+        return out
 
     @classmethod
     def _adopt(cls, handle, nx: int, ny: int, lam: float) -> "ConReg":

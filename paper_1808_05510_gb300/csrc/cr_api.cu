@@ -107,6 +107,13 @@ struct cr_problem {
   int cv_cap = 0;
   double *cv_X = nullptr, *cv_Y = nullptr, *cv_T1 = nullptr, *cv_T2 = nullptr, *cv_P = nullptr, *cv_out = nullptr;
   uint8_t* cv_Om = nullptr;
+  // post-processing (cr_svd_factors, cr_solution_report): P = U Z, reference factors
+  // for post_ref_cap columns, the statistics' partial rows, a column block of W
+  double *post_P = nullptr, *post_part = nullptr, *post_out = nullptr, *post_W = nullptr;
+  double *post_Ur = nullptr, *post_Zr = nullptr, *post_Vr = nullptr, *post_Pr = nullptr;
+  double *post_small = nullptr, *post_Uh = nullptr, *post_Vh = nullptr;
+  int post_ref_cap = 0;
+  int64_t post_part_cap = 0, post_W_cols = 0;
   int64_t fcg_fallbacks = 0, learned_solves = 0, mixed_handovers = 0;
   // grid-wide PCG (grids the register-resident kernel does not take, or pcg_kernel = 2): work buffers
   double *pg_work = nullptr, *pg_part = nullptr, *pg_ypart = nullptr, *pg_yglob = nullptr;
@@ -1228,6 +1235,103 @@ cr_status do_rank_one(cr_problem* p, cr_rank1_info* info) {
   return CR_OK;
 }
 
+// One-sided Jacobi SVD of an n x n matrix A (column-major), the method of
+// Hestenes (1958), accurate in the relative sense shown by Demmel and Veselic
+// (1992).  Plane rotations applied from the right make A's columns mutually
+// orthogonal, A J1 J2 ... = U~ S; their product is V~.  A pair (p, q) is left
+// alone once |a_p^T a_q| <= sqrt(n) eps |a_p| |a_q|, and the sweeps stop after
+// one without a rotation.  On return A holds U~ (unit columns), s the singular
+// values and V the columns of V~, ordered by descending s.  Columns of U~ whose
+// singular value is exactly zero are completed to an orthonormal set.
+void jacobi_svd(int n, std::vector<double>& A, std::vector<double>& s, std::vector<double>& V) {
+  V.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) V[i + (size_t)i * n] = 1.0;
+  constexpr double eps = 2.220446049250313e-16;
+  const double tol = eps * std::sqrt((double)std::max(n, 1));
+  auto col = [n](std::vector<double>& M, int c) { return M.data() + (size_t)c * n; };
+  for (int sweep = 0; sweep < 80; ++sweep) {
+    bool rotated = false;
+    for (int pp = 0; pp < n - 1; ++pp)
+      for (int qq = pp + 1; qq < n; ++qq) {
+        double* x = col(A, pp);
+        double* y = col(A, qq);
+        double a = 0.0, b = 0.0, g = 0.0;
+        for (int k = 0; k < n; ++k) {
+          a += x[k] * x[k];
+          b += y[k] * y[k];
+          g += x[k] * y[k];
+        }
+        if (g == 0.0 || std::fabs(g) <= tol * std::sqrt(a * b)) continue;
+        rotated = true;
+        // (c, s) with c^2 - s^2 = ((b - a) / g) c s: the smaller root t = s / c
+        const double zeta = (b - a) / (2.0 * g);
+        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), sn = c * t;
+        for (int k = 0; k < n; ++k) {
+          const double xk = x[k], yk = y[k];
+          x[k] = c * xk - sn * yk;
+          y[k] = sn * xk + c * yk;
+        }
+        double* vx = col(V, pp);
+        double* vy = col(V, qq);
+        for (int k = 0; k < n; ++k) {
+          const double xk = vx[k], yk = vy[k];
+          vx[k] = c * xk - sn * yk;
+          vy[k] = sn * xk + c * yk;
+        }
+      }
+    if (!rotated) break;
+  }
+  s.assign(n, 0.0);
+  for (int c = 0; c < n; ++c) {
+    double* x = col(A, c);
+    double nr = 0.0;
+    for (int k = 0; k < n; ++k) nr += x[k] * x[k];
+    s[c] = std::sqrt(nr);
+    if (s[c] > 0.0)
+      for (int k = 0; k < n; ++k) x[k] /= s[c];
+  }
+  std::vector<int> order(n);
+  for (int c = 0; c < n; ++c) order[c] = c;
+  std::stable_sort(order.begin(), order.end(), [&s](int u, int v) { return s[u] > s[v]; });
+  std::vector<double> A2((size_t)n * n), V2((size_t)n * n), s2(n);
+  for (int c = 0; c < n; ++c) {
+    s2[c] = s[order[c]];
+    std::copy(col(A, order[c]), col(A, order[c]) + n, A2.data() + (size_t)c * n);
+    std::copy(col(V, order[c]), col(V, order[c]) + n, V2.data() + (size_t)c * n);
+  }
+  A.swap(A2);
+  V.swap(V2);
+  s.swap(s2);
+  // zero singular values sort last: each of their left vectors becomes the unit
+  // vector with the largest part orthogonal to the columns before it (the parts
+  // of all n unit vectors add up to n - c > 0), orthogonalised twice
+  std::vector<double> x(n), best(n);
+  for (int c = 0; c < n; ++c) {
+    if (s[c] > 0.0) continue;
+    double best_nr = -1.0;
+    for (int e = 0; e < n; ++e) {
+      std::fill(x.begin(), x.end(), 0.0);
+      x[e] = 1.0;
+      for (int pass = 0; pass < 2; ++pass)
+        for (int d = 0; d < c; ++d) {
+          const double* y = col(A, d);
+          double g = 0.0;
+          for (int k = 0; k < n; ++k) g += y[k] * x[k];
+          for (int k = 0; k < n; ++k) x[k] -= g * y[k];
+        }
+      double nr = 0.0;
+      for (int k = 0; k < n; ++k) nr += x[k] * x[k];
+      if (nr > best_nr) {
+        best_nr = nr;
+        best = x;
+      }
+    }
+    const double inv = 1.0 / std::sqrt(best_nr);
+    for (int k = 0; k < n; ++k) col(A, c)[k] = best[k] * inv;
+  }
+}
+
 }  // namespace
 
 namespace cr {
@@ -1858,6 +1962,133 @@ cr_status cr_cv_error(cr_problem* p, int32_t mt, const double* Xt, int64_t ldx, 
   TRY(sync(p));
   *num = out[0];
   *den = out[1];
+  return CR_OK;
+}
+
+cr_status cr_svd_factors(cr_problem* p, double* Uh, int64_t ldu, double* sigma, double* Vh, int64_t ldv) {
+  if (!p) return CR_EINVAL;
+  const int j = p->j, ny = p->ny, nx = p->nx;
+  if (j == 0) return CR_OK;
+  if ((Uh && ldu < ny) || (Vh && ldv < nx)) return fail(p, CR_EINVAL, "leading dimension");
+  cudaStream_t st = p->st;
+  // the core Z to the host, its SVD there (j x j), then U^ = U U~ and V^ = V V~ on the device
+  std::vector<double> A((size_t)j * j), s, Vt;
+  CUCHK(p, cudaMemcpy2DAsync(A.data(), j * sizeof(double), p->Z, (size_t)p->rcap * sizeof(double),
+                             j * sizeof(double), j, cudaMemcpyDeviceToHost, st));
+  p->d2h_bytes += (int64_t)sizeof(double) * j * j;
+  TRY(sync(p));
+  jacobi_svd(j, A, s, Vt);
+  if (sigma) std::copy(s.begin(), s.end(), sigma);
+  if (!Uh && !Vh) return CR_OK;
+  if (!p->post_small) TRY(dalloc(p, &p->post_small, (size_t)2 * p->rcap * p->rcap));
+  double* dUt = p->post_small;
+  double* dVt = p->post_small + (size_t)p->rcap * p->rcap;
+  if (Uh) {
+    if (!p->post_Uh) TRY(dalloc(p, &p->post_Uh, (size_t)ny * p->rcap));
+    CUCHK(p, cudaMemcpyAsync(dUt, A.data(), sizeof(double) * j * j, cudaMemcpyHostToDevice, st));
+    gemm(ny, j, j, 1.0, MatView{p->UU, 1, 3 * (int64_t)ny}, MatView{dUt, 1, j}, 0.0, p->post_Uh, 1, ny, p->ws,
+         p->ws_elems, st);
+    CUCHK(p, cudaMemcpy2DAsync(Uh, ldu * sizeof(double), p->post_Uh, ny * sizeof(double), ny * sizeof(double), j,
+                               cudaMemcpyDeviceToHost, st));
+    p->h2d_bytes += (int64_t)sizeof(double) * j * j;
+    p->d2h_bytes += (int64_t)sizeof(double) * ny * j;
+  }
+  if (Vh) {
+    if (!p->post_Vh) TRY(dalloc(p, &p->post_Vh, (size_t)nx * p->rcap));
+    CUCHK(p, cudaMemcpyAsync(dVt, Vt.data(), sizeof(double) * j * j, cudaMemcpyHostToDevice, st));
+    gemm(nx, j, j, 1.0, MatView{p->VV, 1, 3 * (int64_t)nx}, MatView{dVt, 1, j}, 0.0, p->post_Vh, 1, nx, p->ws,
+         p->ws_elems, st);
+    CUCHK(p, cudaMemcpy2DAsync(Vh, ldv * sizeof(double), p->post_Vh, nx * sizeof(double), nx * sizeof(double), j,
+                               cudaMemcpyDeviceToHost, st));
+    p->h2d_bytes += (int64_t)sizeof(double) * j * j;
+    p->d2h_bytes += (int64_t)sizeof(double) * nx * j;
+  }
+  return sync(p);
+}
+
+cr_status cr_solution_report(cr_problem* p, int32_t nonneg, int32_t jr, const double* Ur, int64_t ldur,
+                             const double* Zr, int64_t ldzr, const double* Vr, int64_t ldvr, double* W, int64_t ldw,
+                             cr_solution_stats* out) {
+  if (!p || !out) return CR_EINVAL;
+  *out = cr_solution_stats{};
+  const int ny = p->ny, nx = p->nx, j = p->j;
+  if (jr < 0) return fail(p, CR_EINVAL, "reference rank below zero");
+  if (jr > 0 && (!Ur || !Zr || !Vr || ldur < ny || ldzr < jr || ldvr < nx))
+    return fail(p, CR_EINVAL, "reference factors: null pointer or leading dimension too small");
+  if (W && ldw < ny) return fail(p, CR_EINVAL, "leading dimension of W");
+  cudaStream_t st = p->st;
+  out->entries = (int64_t)ny * nx;
+  if (out->entries == 0) return CR_OK;
+  // P = U Z (ny x j); U's columns sit every third column of the interleaved panel
+  if (!p->post_P) TRY(dalloc(p, &p->post_P, (size_t)ny * p->rcap));
+  if (j > 0)
+    gemm(ny, j, j, 1.0, MatView{p->UU, 1, 3 * (int64_t)ny}, MatView{p->Z, 1, p->rcap}, 0.0, p->post_P, 1, ny, p->ws,
+         p->ws_elems, st);
+  if (jr > 0) {
+    if (jr > p->post_ref_cap) {
+      const int c = std::max(jr, p->rcap);
+      TRY(dalloc(p, &p->post_Ur, (size_t)ny * c));
+      TRY(dalloc(p, &p->post_Zr, (size_t)c * c));
+      TRY(dalloc(p, &p->post_Vr, (size_t)nx * c));
+      TRY(dalloc(p, &p->post_Pr, (size_t)ny * c));
+      p->post_ref_cap = c;
+    }
+    CUCHK(p, cudaMemcpy2DAsync(p->post_Ur, ny * sizeof(double), Ur, ldur * sizeof(double), ny * sizeof(double), jr,
+                               cudaMemcpyHostToDevice, st));
+    CUCHK(p, cudaMemcpy2DAsync(p->post_Zr, jr * sizeof(double), Zr, ldzr * sizeof(double), jr * sizeof(double), jr,
+                               cudaMemcpyHostToDevice, st));
+    CUCHK(p, cudaMemcpy2DAsync(p->post_Vr, nx * sizeof(double), Vr, ldvr * sizeof(double), nx * sizeof(double), jr,
+                               cudaMemcpyHostToDevice, st));
+    p->h2d_bytes += (int64_t)sizeof(double) * jr * ((int64_t)ny + nx + jr);
+    gemm(ny, jr, jr, 1.0, MatView{p->post_Ur, 1, ny}, MatView{p->post_Zr, 1, jr}, 0.0, p->post_Pr, 1, ny, p->ws,
+         p->ws_elems, st);
+  }
+  // without W on the host one launch covers every column; with it, blocks of
+  // columns go through a device buffer of at most kPostBlockBytes
+  constexpr int64_t kPostBlockBytes = (int64_t)256 << 20;
+  int64_t cw = nx;
+  if (W) {
+    cw = std::max<int64_t>(64, kPostBlockBytes / ((int64_t)sizeof(double) * ny) / 64 * 64);
+    cw = std::min<int64_t>(cw, nx);
+    if (cw > p->post_W_cols) {
+      TRY(dalloc(p, &p->post_W, (size_t)ny * cw));
+      p->post_W_cols = cw;
+    }
+  }
+  int64_t nparts = 0;
+  for (int64_t c0 = 0; c0 < nx; c0 += cw) nparts += post_tiles_parts(ny, (int)std::min<int64_t>(cw, nx - c0));
+  if (nparts > p->post_part_cap) {
+    TRY(dalloc(p, &p->post_part, (size_t)nparts * PS_N));
+    p->post_part_cap = nparts;
+  }
+  if (!p->post_out) TRY(dalloc(p, &p->post_out, PS_N));
+  int64_t off = 0;
+  for (int64_t c0 = 0; c0 < nx; c0 += cw) {
+    const int ncols = (int)std::min<int64_t>(cw, nx - c0);
+    post_tiles(ny, j, p->post_P, ny, p->VV, 3 * (int64_t)nx, jr, p->post_Pr, ny, p->post_Vr, nx, nonneg ? 1 : 0,
+               (int)c0, ncols, W ? p->post_W : nullptr, ny, p->post_part + off * PS_N, st);
+    off += post_tiles_parts(ny, ncols);
+    if (W) {
+      CUCHK(p, cudaMemcpy2DAsync(W + c0 * ldw, ldw * sizeof(double), p->post_W, ny * sizeof(double),
+                                 ny * sizeof(double), ncols, cudaMemcpyDeviceToHost, st));
+      p->d2h_bytes += (int64_t)sizeof(double) * ny * ncols;
+    }
+  }
+  post_reduce((int)off, p->post_part, p->post_out, st);
+  double r[PS_N];
+  CUCHK(p, cudaMemcpyAsync(r, p->post_out, sizeof(r), cudaMemcpyDeviceToHost, st));
+  p->d2h_bytes += (int64_t)sizeof(r);
+  TRY(sync(p));
+  out->n_negative = (int64_t)r[PS_NNEG];
+  out->w_min = r[PS_MIN];
+  out->w_max = r[PS_MAX];
+  out->w_fro2 = r[PS_W2];
+  out->neg_fro2 = r[PS_NEG2];
+  out->ref_fro2 = r[PS_REF2];
+  out->diff_fro2 = r[PS_DIFF2];
+  out->diff_maxabs = r[PS_MAXABS];
+  out->rms = std::sqrt(r[PS_DIFF2] / (double)out->entries);
+  out->rel = r[PS_REF2] > 0.0 ? std::sqrt(r[PS_DIFF2] / r[PS_REF2]) : std::nan("");
   return CR_OK;
 }
 

@@ -219,6 +219,23 @@ void omega_times(int n, int m, const uint8_t* Om, int64_t ldo, const double* u, 
 void mat_dot(int r, int c, const double* A, int64_t lda, const double* B, int64_t ldb, double* out, cudaStream_t st);
 // out[0] = sum Om (P - Y)^2, out[1] = sum Om Y^2 over n x m (P, Y, Om contiguous, ld n)
 void cv_err(int n, int m, const double* P, const double* Y, const uint8_t* Om, double* out, cudaStream_t st);
+
+// ---------------------------------------------------------------- cr_post.cu
+// Statistics of the solution pass, in slot order: count of negative entries of
+// W, min and max entry, |W|^2, |min(0, W)|^2, |W*|^2, |P(W) - W*|^2, max |P(W) - W*|.
+enum { PS_NNEG, PS_MIN, PS_MAX, PS_W2, PS_NEG2, PS_REF2, PS_DIFF2, PS_MAXABS, PS_N };
+// resident CTAs of the pass on this GPU; partial rows of one post_tiles launch
+int post_blocks();
+int post_tiles_parts(int ny, int ncols);
+// Columns [col0, col0 + ncols) of W = P V^T (P = U Z: ny x j, ld ldp; V(c, k) at
+// V[c + k ldv]) against W* = Pr Vr^T (jr = 0: W* = 0); P(W) = max(0, W) if nonneg.
+// Writes post_tiles_parts(ny, ncols) rows of PS_N statistics to part, and P(W)
+// to out (column c at out + (c - col0) ldo) unless out is null.
+void post_tiles(int ny, int j, const double* P, int64_t ldp, const double* V, int64_t ldv, int jr,
+                const double* Pr, int64_t ldpr, const double* Vr, int64_t ldvr, int nonneg, int col0, int ncols,
+                double* out, int64_t ldo, double* part, cudaStream_t st);
+// out[0..PS_N) = the fixed-order combination of nparts rows of statistics
+void post_reduce(int nparts, const double* part, double* out, cudaStream_t st);
 // out[0] = |Z - Zp|_F^2, out[1] = |Z|_F^2 over j x j
 void mat_diff_norms(int j, const double* Z, const double* Zp, int64_t ld, double* out, cudaStream_t st);
 // C = alpha A + beta B (r x c); B may alias C

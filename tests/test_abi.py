@@ -97,7 +97,7 @@ def test_destroy_null_is_noop(lib):
 
 
 STRUCTS = ["cr_csr", "cr_problem_desc", "cr_options", "cr_rank1_info", "cr_proj_info", "cr_stats", "cr_solve_info",
-           "cr_member", "cr_member_result"]
+           "cr_member", "cr_member_result", "cr_solution_stats"]
 
 
 def test_struct_layouts_match_header(tmp_path):
