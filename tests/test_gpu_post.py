@@ -179,13 +179,20 @@ def test_visual_cortex_full_size_blocks_and_determinism(cr):
     with cr.ConReg.from_problem(p, r_cap=j) as g:
         g.cr_set_factors(U, Z, V)
         r = g.cr_solution_report(nonneg=True, ref=ref, want_w=True)
-        again = g.cr_solution_report(nonneg=True, ref=ref, want_w=False)
+        again = g.cr_solution_report(nonneg=True, ref=ref, want_w=True)
+        one = g.cr_solution_report(nonneg=True, ref=ref, want_w=False)  # one launch over all columns
         Uh, s, Vh = g.cr_svd_factors()
     W_max = max(abs(o["w_min"]), abs(o["w_max"]))
     check_report(r, o, W_max)
+    check_report(one, o, W_max)
     assert np.abs(r["W_out"] - o["W_out"]).max() <= 1e-12 * W_max
+    assert np.array_equal(again["W_out"], r["W_out"])
     for k in ("n_negative", "w_min", "w_max", "w_fro2", "neg_fro2", "ref_fro2", "diff_fro2", "diff_maxabs"):
         assert again[k] == r[k], k
+    # the blocked and the one-launch pass split the tiles differently: same
+    # entries, extremes and count; sums equal up to their order
+    for k in ("n_negative", "w_min", "w_max", "diff_maxabs"):
+        assert one[k] == r[k], k
     so = post.solution_svd(U, Z, V)[1]
     assert np.abs(s - so).max() <= 1e-13 * so[0]
 
