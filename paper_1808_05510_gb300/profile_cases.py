@@ -7,6 +7,10 @@
         two Galerkin projections (Eq. Proj_Sylv) at rank 60 from a float64 greedy run
     python -m paper_1808_05510_gb300.profile_cases assembly tc
         three tensor-core assemblies of G_a = U^T diag(Omega_a) U at rank 100
+    python -m paper_1808_05510_gb300.profile_cases post fp64
+        three solution passes (W = U Z V^T in float64 tiles, projected onto W >= 0,
+        statistics only) at rank 100 with random orthonormal U, V; prints the
+        CUDA-event time of each call
     python -m paper_1808_05510_gb300.profile_cases pcg_stress fp32|fp64 [solves]
         u-side ALS solves on the ~4M-voxel stress shell (grid-wide PCG, vectors in
         HBM): fp32 = one float32 grid solve to 1e-5 inside the mixed form's
@@ -69,6 +73,31 @@ def assembly(form: str) -> None:
         print("assembled", G.shape, flush=True)
 
 
+def post(form: str) -> None:
+    import torch
+
+    from . import synth
+    from .conreg import ConReg
+
+    p = synth.visual_cortex()
+    j = 100
+    rng = np.random.default_rng(11)
+    U, _ = np.linalg.qr(rng.standard_normal((p.ny, j)))
+    V, _ = np.linalg.qr(rng.standard_normal((p.nx, j)))
+    Z = rng.standard_normal((j, j))
+    with ConReg.from_problem(p, r_cap=j) as g:
+        g.cr_set_factors(U, Z, V)
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(g.stream)
+            r = g.cr_solution_report(nonneg=True)
+            e1.record(g.stream)
+            e1.synchronize()
+            print(f"entries {r['entries']} negative {r['n_negative']} call_ms {e0.elapsed_time(e1):.3f}", flush=True)
+
+
 def pcg_stress(form: str, solves: int = 2) -> None:
     import torch
 
@@ -102,4 +131,4 @@ if __name__ == "__main__":
     if case == "pcg_stress":
         pcg_stress(form, int(sys.argv[3]) if len(sys.argv) > 3 else 2)
     else:
-        {"pcg": pcg, "galerkin": galerkin, "assembly": assembly}[case](form)
+        {"pcg": pcg, "galerkin": galerkin, "assembly": assembly, "post": post}[case](form)
