@@ -72,7 +72,7 @@ def workload(args, rank=0):
     cfg = {
         "workload": "visual-cortex-shaped synthetic: smooth random blob mask in a 40^3 box, 7-point Laplacians",
         "ny": p.ny, "nx": p.nx, "ninj": p.m, "lambda": p.lam, "r_max": args.r_max, "tau": args.tau,
-        "relres_target": args.relres, "precision": args.precision, "pcg_tol": 1e-10, "pcg_tol_mixed": "1e-10 (float32 inner solves to 1e-5 under float64 refinement)",
+        "relres_target": args.relres, "precision": args.precision, "pcg_tol": 1e-10, "pcg_tol_mixed": "1e-10 (float32 inner solves to max(1e-5, what the float64 target still needs / 2) under float64 refinement)",
         "l2": "flushed between steps (256 MiB write)", "parallelism": "replicas",
     }
     return p, cfg

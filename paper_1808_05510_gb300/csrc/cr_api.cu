@@ -715,7 +715,7 @@ cr_status launch_pcg_jacobi(cr_problem* p, int side, const double* b, double* x,
 // float32 cluster PCG.  Each outer step forms the float64 residual
 // r = b - A_hat x, stops once |r| <= pcg_tol |b|, and otherwise solves
 // A_hat d = r from d = 0 in float32 (inner products in double-float) to
-// kMixedInnerTol relative, then x += d.  An outer step that does not cut |r|
+// max(kMixedInnerTol, pcg_tol |b| / (2 |r|)) relative, then x += d.  An outer step that does not cut |r|
 // by 4x (float32 cannot resolve the system, e.g. at very large lambda) or the
 // step cap hands the solve over to the float64 kernel from the current x, so
 // the result meets the float64 tolerance either way.
@@ -754,7 +754,10 @@ cr_status launch_pcg_mixed(cr_problem* p, int side, const double* b, double* x, 
     }
     rr_prev = rr;
     fill(n, 0.0, d, st);
-    TRY(run_pcg(p, side, r, d, maxit - total, kMixedInnerTol, true));
+    // an inner solve never goes further than the float64 target needs (with a
+    // factor 2 to spare): on warm-started sweeps the last step is much shorter
+    const double inner = std::max(kMixedInnerTol, 0.5 * std::sqrt(tol * tol * bb / rr));
+    TRY(run_pcg(p, side, r, d, maxit - total, inner, true));
     TRY(readback(p, 0, 1, true));
     const PcgStat in = p->hs->stat[side];
     total += in.iters;
