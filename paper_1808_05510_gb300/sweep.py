@@ -13,6 +13,7 @@ the library; this module only times calls and aggregates their results.
 from __future__ import annotations
 
 import itertools
+import math
 import time
 from typing import Dict, List, Optional, Sequence, Tuple
 
@@ -68,7 +69,8 @@ def cv_summary(members, results) -> Dict:
         a[0] += r["cv_num"]
         a[1] += r["cv_den"]
     curve = {lam: (v[0] / v[1] if v[1] > 0 else float("nan")) for lam, v in sorted(per.items())}
-    best = min(curve, key=lambda lam: curve[lam]) if curve else None
+    scored = [lam for lam, e in curve.items() if not math.isnan(e)]  # NaN: no observed held-out entry
+    best = min(scored, key=lambda lam: curve[lam]) if scored else None
     return {"cv_by_lambda": curve, "best_lambda": best}
 
 
