@@ -167,6 +167,8 @@ typedef struct {
   int64_t learned_fallbacks;      /* learned solves that stagnated and were finished by Jacobi-PCG */
   int64_t learned_off;            /* bit s set: the learned form is switched off for side s */
   int64_t mixed_handovers;        /* mixed-form sub-solves that float32 refinement handed to float64 */
+  int64_t pcg_cluster[2];         /* CTAs per thread-block cluster of the u-side (0) and v-side (1) PCG;
+                                     0 = the grid-wide kernel */
 } cr_stats;
 
 /* Fill *o with defaults (struct_size set).  Always succeeds for o != NULL. */
@@ -245,7 +247,7 @@ cr_status cr_galerkin_assembly(struct cr_problem* p, int32_t method, float* G_ho
  * after reading.  Synchronises the problem's stream. */
 cr_status cr_get_stats(struct cr_problem* p, cr_stats* s, int32_t reset);
 
-/* Allocation-free solve of Eq. (ALS_linsys)-type systems, for callers that
+/* Allocation-free solve of the library's u-side ALS system, for callers that
  * cannot allocate device memory (a plug-in confined to buffers its host
  * application hands it, code that must not enter the allocator, a process whose
  * allocator belongs to another runtime).  The paper has no counterpart: it is
@@ -261,11 +263,13 @@ cr_status cr_get_stats(struct cr_problem* p, cr_stats* s, int32_t reset);
  * It allocates nothing: its work vectors live in one static device array of
  * 5 x 131072 doubles (about 5 MiB) that every GPU loading the library keeps
  * until the process exits, so n may be at most 131072 (larger n: CR_EINVAL).
- * The first call on each device looks up that array's device address (with the
- * device current); make it before any stream capture.  All calls share the
- * array: calls whose kernels overlap on the GPU (other streams or host threads)
- * race and return garbage.  Synchronises `stream`.  Errors are described by
- * cr_last_error(NULL). */
+ * Every call looks up that array's device address in the current context
+ * (with the device current); the first call on a device also loads the
+ * library's device code there, so make it before any stream capture.  All
+ * calls share the array: calls whose kernels overlap on the GPU (other streams
+ * or host threads) race and return garbage.  The call waits for `stream` to
+ * finish before it returns (it reads its status words back).  Errors are
+ * described by cr_last_error(NULL). */
 cr_status cr_solve_u_noalloc(int64_t n, const int32_t* rowptr_dev, const int32_t* col_dev, const double* val_dev,
                              double lambda, double c, double d, const double* omega_dev, const double* rhs_dev,
                              double* u_hat_dev, double tol, int32_t maxit, int32_t* iters, void* stream);

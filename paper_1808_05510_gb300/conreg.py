@@ -70,7 +70,7 @@ class cr_stats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("pcg_solves", C.c_int64), ("pcg_iters", C.c_int64),
                 ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("phase_ms", C.c_double * 8), ("phase_calls", C.c_int64 * 8),
                 ("learned_solves", C.c_int64), ("learned_fallbacks", C.c_int64), ("learned_off", C.c_int64),
-                ("mixed_handovers", C.c_int64)]
+                ("mixed_handovers", C.c_int64), ("pcg_cluster", C.c_int64 * 2)]
 
 
 class cr_solve_info(C.Structure):
@@ -426,25 +426,34 @@ class ConReg:
                 "phase_ms": {PHASES[i]: s.phase_ms[i] for i in range(8)},
                 "phase_calls": {PHASES[i]: s.phase_calls[i] for i in range(8)},
                 "learned_solves": s.learned_solves, "learned_fallbacks": s.learned_fallbacks,
-                "learned_off": s.learned_off, "mixed_handovers": s.mixed_handovers}
+                "learned_off": s.learned_off, "mixed_handovers": s.mixed_handovers,
+                "pcg_cluster": [s.pcg_cluster[0], s.pcg_cluster[1]]}
 
-    def cr_solve_u(self, v, rhs):
+    def cr_solve_u(self, v, rhs, allow_notconv: bool = False):
+        """(solution, iterations); with ``allow_notconv`` a solve that stopped at
+        pcg_maxit returns (best iterate, iterations, status) instead of raising."""
         v = np.ascontiguousarray(v, dtype=np.float64)
         rhs = np.ascontiguousarray(rhs, dtype=np.float64)
         out = np.zeros(self.ny)
         it = C.c_int32()
         st = self._lib.cr_solve_u(self.h, _ptr(v), _ptr(rhs), _ptr(out), C.byref(it))
+        if allow_notconv and st == CR_ENOTCONV:
+            return out, it.value, st
         _check(st, self.h, "cr_solve_u")
-        return out, it.value
+        return (out, it.value, st) if allow_notconv else (out, it.value)
 
-    def cr_solve_v(self, u, rhs):
+    def cr_solve_v(self, u, rhs, allow_notconv: bool = False):
+        """(solution, iterations); with ``allow_notconv`` a solve that stopped at
+        pcg_maxit returns (best iterate, iterations, status) instead of raising."""
         u = np.ascontiguousarray(u, dtype=np.float64)
         rhs = np.ascontiguousarray(rhs, dtype=np.float64)
         out = np.zeros(self.nx)
         it = C.c_int32()
         st = self._lib.cr_solve_v(self.h, _ptr(u), _ptr(rhs), _ptr(out), C.byref(it))
+        if allow_notconv and st == CR_ENOTCONV:
+            return out, it.value, st
         _check(st, self.h, "cr_solve_v")
-        return out, it.value
+        return (out, it.value, st) if allow_notconv else (out, it.value)
 
 
 def solve_batch(p, members, r_max: int, tau: float = 0.0, relres_target: float = 0.0, concurrency: int = 0,

@@ -379,7 +379,10 @@ cr_status build_lap(cr_problem* p, const cr_csr& c, DevLap& L) {
   if (cs == 0) {
     // too large for one cluster: the sub-solves run on the grid-wide PCG
     chunk = n;
-  } else if (p->opt.cluster_size > 0 && p->opt.cluster_size < cs) {
+  } else if (p->opt.cluster_size > 0 && p->opt.cluster_size != cs && p->opt.cluster_size <= kMaxCluster &&
+             p->opt.cluster_size <= n) {
+    // a requested cluster size replaces the automatic one when the chunks fit
+    // (smaller or larger than automatic; CTAs past the last row hold no rows)
     const int c2 = p->opt.cluster_size;
     const int ch = (n + c2 - 1) / c2;
     if (pcg_smem_bytes(ch, p->m) <= smem_cap && pcg_cluster_ok(c2, pcg_smem_bytes(ch, p->m))) {
@@ -809,9 +812,6 @@ cr_status grow_projections(cr_problem* p, int q) {
   double* vq = p->VV + (size_t)3 * q * nx;
   lap_apply(p->Ly, uq, uq + ny, 0.0, st);
   lap_apply(p->Ly, uq + ny, uq + 2 * ny, 0.0, st);
-  if (p->ubhi && q < 128)
-    bf16_split(ny, 1, uq, ny, (uint16_t*)p->ubhi + (size_t)q * p->ldb, (uint16_t*)p->ublo + (size_t)q * p->ldb, p->ldb,
-               st);
   lap_apply(p->Lx, vq, vq + nx, 0.0, st);
   lap_apply(p->Lx, vq + nx, vq + 2 * nx, 0.0, st);
   const int64_t ldu = 3 * (int64_t)ny, ldv = 3 * (int64_t)nx;
@@ -838,12 +838,15 @@ cr_status grow_projections(cr_problem* p, int q) {
 // K (the paper's CG is unpreconditioned; the iterate it converges to is the
 // same Galerkin solution).  Device scalars: gs[k & 1] = <R_k, D^-1 R_k>,
 // gs[2] = <P, K P>, gs[3] = |F|^2, gs[4] = |R|^2.
-// float32 G_a = U^T diag(Omega_a) U for the inner solves of the mixed form:
-// re-assembled on the tensor cores from the BF16 shadows of U when j <= 128,
-// else converted from the float64 G that the projections maintain.
-cr_status mixed_G(cr_problem* p, bool force_f64 = false) {
+// float32 G_a = U^T diag(Omega_a) U.  The inner solves of the mixed form take
+// the float64 G that the projections keep up to date by borders, rounded to
+// float32 (one pass over m j^2 words, and exact to float32 rounding).  A full
+// re-assembly from U alone runs on the tensor cores (tcgen05, BF16 hi/lo
+// shadows of U split here, j <= 128) when asked for (cr_galerkin_assembly).
+cr_status mixed_G(cr_problem* p, bool tensor_cores = false) {
   const int64_t ld = p->rcap;
-  if (!force_f64 && p->ubhi && p->j <= 128) {
+  if (tensor_cores && p->ubhi && p->j <= 128) {
+    bf16_split(p->ny, p->j, p->UU, 3 * (int64_t)p->ny, p->ubhi, p->ublo, p->ldb, p->st);
     const cudaError_t e = galerkin_assemble_tc(p->ny, p->j, p->m, p->ubhi, p->ublo, p->ldb, p->Om, p->ny, p->tc_splits,
                                                p->tcpart, p->fG, ld, p->tcerr, p->st);
     if (e == cudaSuccess) return CR_OK;
@@ -1125,6 +1128,7 @@ cr_status do_rank_one(cr_problem* p, cr_rank1_info* info) {
   int sweeps = 0;
   double delta = INFINITY, un = 0.0, vn = 0.0, worst = 0.0;
   int itu = 0, itv = 0;
+  bool capped = false;  // some sub-solve of some sweep stopped at pcg_maxit
   for (;;) {
     prof_begin(p, CR_PHASE_RHS);
     prep_u(p, p->v);
@@ -1147,6 +1151,7 @@ cr_status do_rank_one(cr_problem* p, cr_rank1_info* info) {
     itu += s[0].iters;
     itv += s[1].iters;
     worst = std::max(worst, std::max(s[0].relres, s[1].relres));
+    capped = capped || s[0].status == 1 || s[1].status == 1;
     un = std::sqrt(p->hs->ds[DS_UN2]);
     vn = std::sqrt(p->hs->ds[DS_VN2]);
     ++sweeps;
@@ -1186,9 +1191,7 @@ cr_status do_rank_one(cr_problem* p, cr_rank1_info* info) {
     info->pcg_iters_v = itv;
     info->pcg_relres_max = worst;
   }
-  int nc = 0;
-  for (int q = 0; q < 2; ++q) nc += p->hs->stat[q].status == 1;
-  if (nc) return fail(p, CR_ENOTCONV, "PCG reached pcg_maxit (the step was still taken)");
+  if (capped) return fail(p, CR_ENOTCONV, "PCG reached pcg_maxit in an ALS sweep (the step was still taken)");
   return CR_OK;
 }
 
@@ -1627,7 +1630,7 @@ cr_status cr_galerkin_assembly(cr_problem* p, int32_t method, float* G_host, int
   if (!p->fG) return fail(p, CR_ESTATE, "the assembly runs in the mixed form (precision = CR_MIXED)");
   if (method == 0 && !(p->ubhi && j <= 128)) return fail(p, CR_EINVAL, "tensor-core assembly needs r_cap <= 128");
   if (p->tcerr) CUCHK(p, cudaMemsetAsync(p->tcerr, 0, sizeof(int), p->st));
-  TRY(mixed_G(p, method != 0));
+  TRY(mixed_G(p, method == 0));
   int herr = 0;
   if (p->tcerr) CUCHK(p, cudaMemcpyAsync(&herr, p->tcerr, sizeof(int), cudaMemcpyDeviceToHost, p->st));
   const int64_t ld = p->rcap;
@@ -1656,6 +1659,10 @@ cr_status cr_get_stats(cr_problem* p, cr_stats* s, int32_t reset) {
   s->learned_fallbacks = p->fcg_fallbacks;
   s->learned_off = (p->learned_off[0] ? 1 : 0) | (p->learned_off[1] ? 2 : 0);
   s->mixed_handovers = p->mixed_handovers;
+  for (int side = 0; side < 2; ++side) {
+    const DevLap& L = side == 0 ? p->Ly : p->Lx;
+    s->pcg_cluster[side] = use_grid_pcg(p, side, p->opt.precision == CR_MIXED) ? 0 : L.csize;
+  }
   for (int i = 0; i < CR_NPHASE; ++i) {
     s->phase_ms[i] = p->phase_ms[i];
     s->phase_calls[i] = p->phase_calls[i];

@@ -12,13 +12,17 @@
 // products, Jacobi diagonal) and its status words live in one file-scope
 // static __device__ array sized for at most kMaxN rows.  Every GPU that loads
 // the library keeps that array (about 5 MiB) until the process exits.  Host
-// code cannot use the array's name as a device address, so the first call on
-// each device (with that device current) looks the address up once with
-// cudaGetSymbolAddress and caches it; make that first call before any stream
-// capture.  All calls share the one array and it keeps the last call's
-// contents: the status words are cleared before each launch, and two calls
-// whose kernels overlap on the GPU (different streams, or several host
-// threads) race on the array and produce garbage.
+// code cannot use the array's name as a device address, so every call (with
+// the device current) looks the address up with cudaGetSymbolAddress and sets
+// the kernel's launch attributes; both are cheap host calls and always refer
+// to the current context, so a cudaDeviceReset between calls leaves nothing
+// stale.  The first call on a device also loads the library's device code
+// there; make that first call before any stream capture.  All calls share the
+// one array and it keeps the last call's contents: the status words are
+// cleared before each launch, and two calls whose kernels overlap on the GPU
+// (different streams, or several host threads) race on the array and produce
+// garbage.  Each call waits for its stream to finish before it returns (it
+// reads the status words back).
 //
 // The operator is the one of the existing u-side solve:
 //   lam [(L + c I)^2 + (d - c^2) I] + diag(omega),
@@ -29,7 +33,6 @@
 
 #include <algorithm>
 #include <cmath>
-#include <mutex>
 #include <string>
 
 #include "conreg.h"
@@ -47,7 +50,6 @@ constexpr int64_t kMaxN = 131072;     // rows (16 CTAs x 8192)
 constexpr int kVecs = 5;              // r, p, s, w, dinv
 constexpr int64_t kStatOff = kVecs * kMaxN;
 constexpr int kThreads = 512;
-constexpr int kMaxDev = 64;
 
 static __device__ __align__(256) double g_scratch[kVecs * kMaxN + 8];
 
@@ -230,37 +232,25 @@ __global__ void __launch_bounds__(kThreads, 1) na_pcg_kernel(const NaArgs A) {
 
 size_t na_smem(int chunk) { return sizeof(double) * (3 * (size_t)chunk + 8 + 128 + 8); }
 
-struct DevState {
-  double* scratch = nullptr;
-  bool ready = false;
-};
-DevState g_dev[kMaxDev];
-std::mutex g_mu;
-
-// Once per device, with that device current: the device address of the
-// scratch array and the kernel's launch attributes.
-cr_status na_setup(int dev, double** out, std::string& err) {
-  std::lock_guard<std::mutex> lk(g_mu);
-  DevState& s = g_dev[dev];
-  if (!s.ready) {
-    void* ptr = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);
-    if (e != cudaSuccess || !ptr) {
-      err = std::string("cudaGetSymbolAddress(scratch) failed: ") + cudaGetErrorString(e);
-      cudaGetLastError();
-      return CR_ECUDA;
-    }
-    e = cudaFuncSetAttribute(na_pcg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(na_pcg_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) {
-      err = std::string("kernel attribute set-up failed: ") + cudaGetErrorString(e);
-      cudaGetLastError();
-      return CR_ECUDA;
-    }
-    s.scratch = static_cast<double*>(ptr);
-    s.ready = true;
+// With the device current: the device address of the scratch array in the
+// current context and the kernel's launch attributes.  Looked up on every call,
+// so nothing cached can outlive a context reset.
+cr_status na_setup(double** out, std::string& err) {
+  void* ptr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);
+  if (e != cudaSuccess || !ptr) {
+    err = std::string("cudaGetSymbolAddress(scratch) failed: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    return CR_ECUDA;
   }
-  *out = s.scratch;
+  e = cudaFuncSetAttribute(na_pcg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(na_pcg_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) {
+    err = std::string("kernel attribute set-up failed: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    return CR_ECUDA;
+  }
+  *out = static_cast<double*>(ptr);
   return CR_OK;
 }
 
@@ -302,13 +292,13 @@ extern "C" cr_status cr_solve_u_noalloc(int64_t n, const int32_t* rowptr_dev, co
   if (!(tol > 0.0) || maxit < 1 || !(lambda > 0.0) || !std::isfinite(c) || !std::isfinite(d))
     return bad(CR_EINVAL, "cr_solve_u_noalloc: bad tol, maxit, lambda, c or d");
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+  if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
     return bad(CR_ECUDA, "cr_solve_u_noalloc: no current CUDA device");
   }
   std::string err;
   double* scratch = nullptr;
-  cr_status s = na_setup(dev, &scratch, err);
+  cr_status s = na_setup(&scratch, err);
   if (s != CR_OK) return bad(s, err);
   const int ni = (int)n;
   int desired = std::min(16, std::max(1, (ni + 479) / 480));

@@ -60,18 +60,32 @@ def autotune(p, members, r_probe: int = 2, candidates: Sequence[Tuple[int, int]]
             "r_probe": r_probe, "table": table}
 
 
+CR_ENOTCONV = 4  # cr_status of a member whose solve stopped at an iteration cap
+
+
 def cv_summary(members, results) -> Dict:
     """Mean held-out error per lambda over its folds (sum of numerators over sum
-    of denominators) and the lambda that minimises it."""
+    of denominators) and the lambda that minimises it.
+
+    A member whose solve stopped at an iteration cap (status CR_ENOTCONV) is
+    scored on an unconverged iterate: ``not_converged`` counts them per lambda,
+    and a lambda with any such fold is left out of the choice of
+    ``best_lambda`` unless no lambda has all its folds converged."""
     per: Dict[float, List[float]] = {}
+    nc: Dict[float, int] = {}
     for (lam, _, _), r in zip(members, results):
         a = per.setdefault(lam, [0.0, 0.0])
         a[0] += r["cv_num"]
         a[1] += r["cv_den"]
+        nc[lam] = nc.get(lam, 0) + (1 if r.get("status", 0) == CR_ENOTCONV else 0)
     curve = {lam: (v[0] / v[1] if v[1] > 0 else float("nan")) for lam, v in sorted(per.items())}
     scored = [lam for lam, e in curve.items() if not math.isnan(e)]  # NaN: no observed held-out entry
-    best = min(scored, key=lambda lam: curve[lam]) if scored else None
-    return {"cv_by_lambda": curve, "best_lambda": best}
+    clean = [lam for lam in scored if nc[lam] == 0]
+    pool = clean if clean else scored
+    best = min(pool, key=lambda lam: curve[lam]) if pool else None
+    return {"cv_by_lambda": curve, "best_lambda": best,
+            "not_converged": {lam: nc[lam] for lam in sorted(nc)},
+            "best_lambda_all_converged": bool(clean)}
 
 
 def run(p, members, r_max: int, tau: float = 1e-9, tune: bool = True, **opts) -> Dict:

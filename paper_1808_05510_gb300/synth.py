@@ -389,6 +389,15 @@ def masked3d(seed: int = 1813, box: int = 12, n_target: int = 700, m: int = 6, l
     return _finish(f"masked3d-{g.n}vox-m{m}", g, g, X, rng, lam, r_max)
 
 
+def box3d(seed: int = 1817, side: int = 50, m: int = 2, lam: float = 50.0, r_max: int = 4) -> Problem:
+    """Full side^3 box (every voxel active, 7-point Laplacian) with m blobs (sigma 2 voxels):
+    a large single-cluster case (125,000 rows at side 50)."""
+    rng = np.random.default_rng(seed)
+    g = Grid(np.ones((side, side, side), dtype=bool))
+    X = gaussian_injections(g, m, rng, 2.0, 2.0, 1.0, 1.0)
+    return _finish(f"box{side}-m{m}", g, g, X, rng, lam, r_max)
+
+
 def paper_toy(seed: int = 1808, n: int = 200, m: int = 5, lam: float = 100.0, noise: float = 0.1,
               quadrature: bool = False) -> Problem:
     """The paper's 1-D toy brain (Sec. 3.1): n-point chain on [0, 1], m box injections of
@@ -421,4 +430,15 @@ WORKLOADS = {
 
 def random_unit(n: int, seed: int) -> np.ndarray:
     v = np.random.default_rng(seed).standard_normal(n)
+    return v / math.sqrt(float(v @ v))
+
+
+def smooth_unit(grid: Grid, seed: int, width: float = 0.25) -> np.ndarray:
+    """Unit vector of a smooth bump on the grid (a Gaussian of ``width`` in unit
+    coordinates around a random active voxel), shaped like the ALS factors of a
+    greedy solve: their sub-systems are the ill-conditioned ones."""
+    rng = np.random.default_rng(seed)
+    c = grid.unit_coords()
+    ctr = c[rng.integers(len(c))]
+    v = np.exp(-((c - ctr) ** 2).sum(axis=1) / (2.0 * width * width))
     return v / math.sqrt(float(v @ v))

@@ -67,3 +67,18 @@ def test_cv_summary_by_hand():
     assert math.isnan(out["cv_by_lambda"][5.0]) and out["best_lambda"] is None
     out = sweep.cv_summary(members([0.5, 5.0], 1), [{"cv_num": 0.0, "cv_den": 0.0}, {"cv_num": 3.0, "cv_den": 4.0}])
     assert math.isnan(out["cv_by_lambda"][0.5]) and out["best_lambda"] == 5.0
+
+
+def test_cv_summary_sets_aside_unconverged_members():
+    """A lambda with a fold that stopped at an iteration cap (CR_ENOTCONV) is
+    counted and not chosen while some lambda has all folds converged."""
+    mem = members([1.0, 10.0], n_folds=2)
+    res = [{"cv_num": n, "cv_den": d, "status": s} for n, d, s in [(1, 4, 0), (1, 4, 0), (1, 8, 4), (1, 8, 0)]]
+    out = sweep.cv_summary(mem, res)
+    assert out["cv_by_lambda"] == {1.0: 0.25, 10.0: 0.125}
+    assert out["not_converged"] == {1.0: 0, 10.0: 1}
+    assert out["best_lambda"] == 1.0 and out["best_lambda_all_converged"]
+    # every lambda has an unconverged fold: the plain minimum, flagged
+    res[0]["status"] = 4
+    out = sweep.cv_summary(mem, res)
+    assert out["best_lambda"] == 10.0 and not out["best_lambda_all_converged"]
