@@ -41,7 +41,7 @@ METRIC = "time-to-rel-residual 1e-6 and rank-1 updates/s, mixed/learned vs plain
 UNIT = "rank-1 updates/s"
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -60,9 +60,21 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-ttr", action="store_true")
     ap.add_argument("--no-post", action="store_true", help="skip the post-processing measurement")
-    ap.add_argument("--batch-r", type=int, default=8, help="rank of every sweep member in the batched form")
+    ap.add_argument("--batch-r", type=int, default=50, help="rank of every sweep member in the batched form")
     ap.add_argument("--learn-steps", type=int, default=200)
-    return ap.parse_args()
+    ap.add_argument("--precond", default="multigrid", choices=["multigrid", "jacobi"],
+                    help="preconditioner of the ALS sub-solves in the headline forms")
+    ap.add_argument("--no-jacobi", action="store_true", help="skip the Jacobi-PCG forms timed beside the headline")
+    ap.add_argument("--ttr-r", type=int, default=500, help="rank cap of the visual-cortex time to relres 1e-6")
+    ap.add_argument("--no-cortex", action="store_true", help="skip the whole-cortex line")
+    ap.add_argument("--cortex-r", type=int, default=300, help="rank cap of the whole-cortex line")
+    ap.add_argument("--cortex-resid-every", type=int, default=10,
+                    help="whole-cortex: evaluate relres every k greedy steps (dW every step)")
+    return ap.parse_args(argv)
+
+
+def parse_args_list(argv):
+    return parse(argv)
 
 
 def workload(args, rank=0):
@@ -165,9 +177,10 @@ def pcg_bytes_per_iter(n: int, slots: int = 6, word: float = 8.0) -> float:
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def oracle_sample(p, args, seconds: float):
+def oracle_sample(p, args, seconds: float, max_steps: int = 0):
     """The CPU float64 oracle (Algorithm 1, its own CG sub-solves) on a bounded
-    sample: greedy steps from W = 0 until `seconds` of work; rank-1 updates/s."""
+    sample: greedy steps from W = 0 until `seconds` of work (or max_steps steps);
+    rank-1 updates/s."""
     from oracle import Oracle
 
     class Stop(Exception):
@@ -179,7 +192,7 @@ def oracle_sample(p, args, seconds: float):
 
     def cb(st, U, Z, V):
         done[0] = st.j
-        if time.perf_counter() - t0 > seconds:
+        if (max_steps and st.j >= max_steps) or (not max_steps and time.perf_counter() - t0 > seconds):
             raise Stop()
 
     try:
@@ -231,13 +244,16 @@ def run_ours(args, rank, world, local_rank):
     p, cfg = workload(args, rank)
     stream = torch.cuda.current_stream()
     l2buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    from paper_1808_05510_gb300.conreg import CR_FP64, CR_MIXED, CR_PRECOND_LEARNED
+    from paper_1808_05510_gb300.conreg import (CR_FP64, CR_MIXED, CR_PRECOND_JACOBI, CR_PRECOND_LEARNED,
+                                               CR_PRECOND_MULTIGRID)
 
-    def measure(prec, net=None, steps=None, warmup=None):
+    head_pc = CR_PRECOND_MULTIGRID if args.precond == "multigrid" else CR_PRECOND_JACOBI
+
+    def measure(prec, net=None, steps=None, warmup=None, precond=None):
         steps = args.steps if steps is None else steps
         warmup = args.warmup if warmup is None else warmup
-        g = ConReg.from_problem(p, r_cap=args.r_max, profile=1, precision=prec,
-                                precond=CR_PRECOND_LEARNED if net is not None else 0)
+        pc = CR_PRECOND_LEARNED if net is not None else (head_pc if precond is None else precond)
+        g = ConReg.from_problem(p, r_cap=args.r_max, profile=1, precision=prec, precond=pc)
         if net is not None:
             g.cr_set_voxel_grid(0, p.grid_y.mask)
             g.cr_set_voxel_grid(1, p.grid_x.mask)
@@ -291,7 +307,10 @@ def run_ours(args, rank, world, local_rank):
         bytes_per_launch = iters_per_launch * pcg_bytes_per_iter(int(0.5 * (p.nx + p.ny)), word=word)
         avg_launch_s = kern_ms / kern_calls / 1e3
         achieved = bytes_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
-        return {"value": value, "ms_per_step": t_max / steps, "steps": steps, "time_to_relres_s": ttr,
+        return {"value": value, "ms_per_step": t_max / steps, "steps": steps, "warmup": warmup,
+                "precond": {CR_PRECOND_JACOBI: "jacobi", CR_PRECOND_LEARNED: "learned (flexible CG, Jacobi judge)",
+                            CR_PRECOND_MULTIGRID: "multigrid"}[pc],
+                "pcg_multigrid_levels": stats["pcg_multigrid"], "time_to_relres_s": ttr,
                 "relres_reached_steps": len(reached), "final_relres": infos[-1]["relres"],
                 "final_rank": infos[-1]["rank"], "stop": infos[-1]["stop_name"],
                 "pcg_iters_per_step": stats["pcg_iters"] / steps,
@@ -307,6 +326,11 @@ def run_ours(args, rank, world, local_rank):
                    if net is not None else {})}
 
     forms = {"fp64": measure(CR_FP64), "mixed": measure(CR_MIXED)}
+    if not args.no_jacobi and head_pc != CR_PRECOND_JACOBI:
+        # the Jacobi-PCG forms beside the headline: what the multigrid preconditioner gains
+        jk = min(args.steps, 3)
+        forms["fp64_jacobi"] = measure(CR_FP64, steps=jk, warmup=1, precond=CR_PRECOND_JACOBI)
+        forms["mixed_jacobi"] = measure(CR_MIXED, steps=jk, warmup=1, precond=CR_PRECOND_JACOBI)
     if not args.no_learned:
         # learned preconditioner: trained once (not timed) on the sub-systems of two
         # other problems of the same family, then the float64 solve with flexible CG
@@ -317,7 +341,7 @@ def run_ours(args, rank, world, local_rank):
         t1 = time.perf_counter()
         net, hist, npairs = learned.train_for(train_probs, [0, 5, 10], steps=args.learn_steps, n_random=2, batch=8)
         t2 = time.perf_counter()
-        lf = measure(CR_FP64, net=net, steps=1, warmup=0)
+        lf = measure(CR_FP64, net=net)
         lf["training"] = {"pairs": npairs, "steps": args.learn_steps, "loss_first": float(np.mean(hist[:10])),
                           "loss_last": float(np.mean(hist[-10:])), "seconds": t2 - t1,
                           "problems": "2 visual-cortex-shaped problems, seeds 1900-1901, ranks 0/5/10, both sides"}
@@ -326,6 +350,10 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_batch:
         forms["batched"] = measure_batch(args, rank, world, dev)
     ttr_toy = None if args.no_ttr else measure_ttr_toy(args)
+    ttr_visual = None if args.no_ttr else measure_ttr(p, args, head_pc, r_cap=args.ttr_r,
+                                                      label="visual-cortex workload (7,530 voxels, 28 injections, "
+                                                            "lambda 100)")
+    cortex = None if args.no_cortex else measure_cortex(args, head_pc)
     post = None if args.no_post else measure_post(p, args, CR_MIXED if args.precision == "mixed" else CR_FP64)
     head = forms[args.precision]
     hbm, peak_kind = peaks()
@@ -342,7 +370,8 @@ def run_ours(args, rank, world, local_rank):
            "config": cfg, "time_to_relres_s": head["time_to_relres_s"], "final_relres": head["final_relres"],
            "final_rank": head["final_rank"], "stop": head["stop"],
            "speedup_vs_fp64": head["value"] / forms["fp64"]["value"],
-           "time_to_relres_toy": ttr_toy, "postprocess": post,
+           "time_to_relres_toy": ttr_toy, "time_to_relres_visual": ttr_visual, "whole_cortex": cortex,
+           "postprocess": post,
            "roofline": roofline, "gpu_launches": head["gpu_launches"], "clocks": head["clocks"],
            "forms": {k: {kk: vv for kk, vv in v.items() if kk not in ("clocks",)} for k, v in forms.items()}}
     prec_e2e = CR_MIXED if args.precision == "mixed" else CR_FP64
@@ -369,9 +398,105 @@ def run_ours(args, rank, world, local_rank):
                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                       "ms_per_step": e_t / args.steps}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = oracle_sample(p, args, args.cpu_seconds)
+        out["cpu_baseline"] = cpu_like_for_like(p, args, prec_e2e, head_pc)
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def measure_ttr(p, args, precond, r_cap: int, label: str, runs: int = 2, resid_every: int = 1):
+    """Time to relative residual 1e-6 (Algorithm 1 from W = 0, stopping at relres <= 1e-6,
+    dW <= tau or the rank cap) for the float64 and mixed forms: CUDA events around
+    cr_solve on an already created problem (creation untimed), median of `runs`
+    after a short warm-up solve."""
+    import numpy as np
+    import torch
+
+    from paper_1808_05510_gb300.conreg import CR_FP64, CR_MIXED, ConReg
+
+    stream = torch.cuda.current_stream()
+    out = {"workload": label, "target": args.relres, "rank_cap": r_cap, "residual_every": resid_every}
+    for name, prec in (("fp64", CR_FP64), ("mixed", CR_MIXED)):
+        times, info = [], None
+        with ConReg.from_problem(p, r_cap=r_cap, precision=prec, precond=precond, residual_every=resid_every,
+                                 profile=1) as g:
+            g.cr_solve(3, args.tau, args.relres)
+            for _ in range(runs):
+                g.cr_set_factors(np.zeros((p.ny, 0)), np.zeros((0, 0)), np.zeros((p.nx, 0)))
+                g.cr_get_stats(reset=True)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                info = g.cr_solve(r_cap, args.tau, args.relres)
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1) / 1e3)
+            st = g.cr_get_stats()
+        sec = float(np.median(times))
+        out[name] = {"seconds": sec, "reached": info["stop_name"] == "relres", "rank": info["rank"],
+                     "relres": info["relres"], "stop": info["stop_name"], "updates_per_s": info["rank"] / sec,
+                     "pcg_iters": info["pcg_iters"], "galerkin_cg_iters": info["cg_iters"],
+                     "phase_ms": {k: round(v, 1) for k, v in st["phase_ms"].items() if v}}
+    out["mixed_speedup"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    return out
+
+
+def measure_cortex(args, precond):
+    """The whole-cortex-shaped workload (ellipsoidal shell of ~45,000 voxels in a
+    96 x 64 x 80 box, 126 injections, lambda 1e3): one greedy solve per form to
+    relres 1e-6 or the rank cap, relres checked every few steps."""
+    from paper_1808_05510_gb300 import synth as _synth
+
+    t0 = time.perf_counter()
+    pc = _synth.whole_cortex()
+    gen = time.perf_counter() - t0
+    out = measure_ttr(pc, args, precond, r_cap=args.cortex_r, runs=1, resid_every=args.cortex_resid_every,
+                      label=f"whole-cortex workload ({pc.ny} voxels in a 96x64x80 shell, {pc.m} injections, "
+                            f"lambda {pc.lam:g})")
+    out["data_gen_s"] = gen
+    return out
+
+
+def cpu_like_for_like(p, args, prec, precond):
+    """The oracle and the GPU on the same work: greedy steps 1..k of the same
+    workload from W = 0 (k: what the oracle finishes in --cpu-seconds), residual
+    evaluated every step on both sides.  The oracle runs as it stands on all host
+    cores and, in a child process limited to one BLAS thread, on one core (its
+    first min(k, 2) steps)."""
+    import numpy as np
+    import torch
+
+    from paper_1808_05510_gb300.conreg import ConReg
+
+    mt = oracle_sample(p, args, args.cpu_seconds)
+    k = max(1, mt["steps"])
+    st = None
+    try:
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        code = ("import json,sys; sys.path.insert(0, %r); import bench; from paper_1808_05510_gb300 import synth; "
+                "a = bench.parse_args_list([]); p = synth.visual_cortex(seed=1810, lam=a.lam, r_max=a.r_max); "
+                "print(json.dumps(bench.oracle_sample(p, a, %r, max_steps=%d)))" % (ROOT, args.cpu_seconds, min(k, 2)))
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        st = json.loads(r.stdout.strip().splitlines()[-1])
+        st["cores"] = 1
+    except Exception as e:  # reported, not fatal
+        st = {"error": str(e)[:200]}
+    stream = torch.cuda.current_stream()
+    with ConReg.from_problem(p, r_cap=max(k, 3), precision=prec, precond=precond) as g:
+        g.cr_solve(min(k, 3), args.tau, args.relres)
+        g.cr_set_factors(np.zeros((p.ny, 0)), np.zeros((0, 0)), np.zeros((p.nx, 0)))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = g.cr_solve(k, args.tau, args.relres)
+        e1.record(stream)
+        e1.synchronize()
+        gsec = e0.elapsed_time(e1) / 1e3
+    mt["single_thread"] = st
+    mt["gpu_same_steps"] = {"steps": info["rank"], "seconds": gsec, "value": info["rank"] / gsec,
+                            "ratio_to_oracle": (info["rank"] / gsec) / mt["value"] if mt["value"] else None}
+    return mt
 
 
 # float64 FMA throughput of GB300 from its unit counts: 152 SMs x 2 FMA per SM

@@ -51,7 +51,12 @@ typedef enum {
  * with BF16 tensor-core assembly of the G_a, inside float64 refinement; the
  * residual norm and stopping test stay float64. */
 typedef enum { CR_FP64 = 0, CR_MIXED = 1 } cr_precision;
-typedef enum { CR_PRECOND_JACOBI = 0, CR_PRECOND_LEARNED = 1 } cr_precond;
+/* Preconditioner of the u/v PCG solves.  CR_PRECOND_MULTIGRID: two V-cycles of
+ * smoothed-aggregation multigrid for L + sigma I per application (the inverse
+ * of lam (L + sigma I)^2, sigma^2 = the Laplacian shift plus the mean data
+ * weight over lam), hierarchy built once from L at cr_create; sizes whose
+ * vectors do not fit one thread-block cluster fall back to Jacobi. */
+typedef enum { CR_PRECOND_JACOBI = 0, CR_PRECOND_LEARNED = 1, CR_PRECOND_MULTIGRID = 2 } cr_precond;
 typedef enum { CR_STOP_NONE = 0, CR_STOP_RMAX = 1, CR_STOP_DW = 2, CR_STOP_RELRES = 3, CR_STOP_RANK = 4 } cr_stop;
 
 /* Square sparse matrix in CSR form (host memory): row i holds entries
@@ -63,6 +68,17 @@ typedef struct {
   const double* val;     /* rowptr[n] */
 } cr_csr;
 
+/* Where the descriptor's arrays live (cr_problem_desc.mem_kind). */
+typedef enum { CR_MEM_HOST = 0, CR_MEM_DEVICE = 1 } cr_mem_kind;
+
+/* Optional voxel box of one side: row i of the Laplacian is the voxel with
+ * linear index box_index[i] = z*H*W + y*W + x of a D x H x W box (dims = {D, H,
+ * W}); indices distinct and inside the box.  box_index = NULL: no grid. */
+typedef struct {
+  int32_t dims[3];
+  const int32_t* box_index;
+} cr_grid;
+
 /* Problem data, Algorithm 1's input line (Sec. 1.1 and Sec. 1.4):
  *  Lx (nx x nx), Ly (ny x ny): symmetric graph Laplacians of the voxel
  *      face-adjacency graphs (Sec. 1.1).  Any symmetric CSR matrix is accepted;
@@ -71,7 +87,15 @@ typedef struct {
  *  Y  (ny x ninj): projection (target) data.
  *  Omega (ny x ninj): 1 where Y is observed, 0 on the injection site.
  *  lambda > 0: the weight of Eq. (obj_fun) (not the rescaled lambda-bar; see
- *      cr_lambda_from_bar).  All pointers are host memory and are copied. */
+ *      cr_lambda_from_bar).
+ *  mem_kind: CR_MEM_HOST (0, the zero-initialised default): every array of the
+ *      descriptor (the CSR arrays of Lx and Ly, X, Y, Omega, the grids' box
+ *      indices) is host memory; CR_MEM_DEVICE: every one of them is device memory
+ *      of the current GPU (not host, not another device: CR_EINVAL).  Either way
+ *      the library copies the inputs at the call (device inputs are staged
+ *      through host memory for validation) and the caller keeps ownership.
+ *  grid_x, grid_y: optional voxel boxes of the two sides (cr_set_voxel_grid at
+ *      creation), used by the learned preconditioner. */
 typedef struct {
   int64_t nx, ny, ninj;
   cr_csr Lx, Ly;
@@ -82,6 +106,8 @@ typedef struct {
   const uint8_t* Omega_host;
   int64_t ldo;
   double lambda;
+  int32_t mem_kind;
+  cr_grid grid_x, grid_y;
 } cr_problem_desc;
 
 /* Solver options; call cr_options_default() first, then override fields. */
@@ -169,6 +195,7 @@ typedef struct {
   int64_t mixed_handovers;        /* mixed-form sub-solves that float32 refinement handed to float64 */
   int64_t pcg_cluster[2];         /* CTAs per thread-block cluster of the u-side (0) and v-side (1) PCG;
                                      0 = the grid-wide kernel */
+  int64_t pcg_multigrid[2];       /* levels of the multigrid preconditioner per side (0 = not in use) */
 } cr_stats;
 
 /* Fill *o with defaults (struct_size set).  Always succeeds for o != NULL. */
@@ -214,6 +241,18 @@ cr_status cr_get_rank(const struct cr_problem* p, int32_t* j);
 /* Copy U (ny x j), Z (j x j), V (nx x j) into caller host buffers (any may be NULL). */
 cr_status cr_get_factors(struct cr_problem* p, double* U_host, int64_t ldu, double* Z_host, int64_t ldz,
                          double* V_host, int64_t ldv);
+
+/* Opaque checkpoint of the iterate between greedy steps (Algorithm 1's loop
+ * state): the rank j, U, Z, V and the Z of the step before (so that dW
+ * continues), tagged with the problem's sizes and lambda.  cr_get_state with
+ * buf = NULL stores the size in *bytes; otherwise *bytes must be at least that
+ * size and the state is written to the host buffer buf.  cr_set_state restores
+ * a state into a problem with the same ny, nx, ninj and lambda (CR_EINVAL
+ * otherwise, or for a corrupt buffer; CR_ESTATE if its rank exceeds r_cap) and
+ * rebuilds every projection, so that continuing from it repeats the original
+ * run bit for bit. */
+cr_status cr_get_state(struct cr_problem* p, void* buf, size_t* bytes);
+cr_status cr_set_state(struct cr_problem* p, const void* buf, size_t bytes);
 
 /* Replace the state by rank j factors (U, V must have orthonormal columns; the
  * library does not re-orthogonalise) and rebuild every projection: checkpoint

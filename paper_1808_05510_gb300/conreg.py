@@ -21,7 +21,7 @@ _lib = None
 
 CR_OK, CR_EINVAL, CR_ENOMEM, CR_ECUDA, CR_ENOTCONV, CR_ETIMEOUT, CR_ERANK, CR_ESTATE = range(8)
 CR_FP64, CR_MIXED = 0, 1
-CR_PRECOND_JACOBI, CR_PRECOND_LEARNED = 0, 1
+CR_PRECOND_JACOBI, CR_PRECOND_LEARNED, CR_PRECOND_MULTIGRID = 0, 1, 2
 STOP_NAMES = {0: "none", 1: "r_max", 2: "dW", 3: "relres", 4: "rank"}
 
 _dp = C.POINTER(C.c_double)
@@ -33,10 +33,18 @@ class cr_csr(C.Structure):
     _fields_ = [("n", C.c_int64), ("rowptr", _ip), ("col", _ip), ("val", _dp)]
 
 
+class cr_grid(C.Structure):
+    _fields_ = [("dims", C.c_int32 * 3), ("box_index", _ip)]
+
+
+CR_MEM_HOST, CR_MEM_DEVICE = 0, 1
+
+
 class cr_problem_desc(C.Structure):
     _fields_ = [("nx", C.c_int64), ("ny", C.c_int64), ("ninj", C.c_int64), ("Lx", cr_csr), ("Ly", cr_csr),
                 ("X_host", _dp), ("ldx", C.c_int64), ("Y_host", _dp), ("ldy", C.c_int64),
-                ("Omega_host", _up), ("ldo", C.c_int64), ("lambda_", C.c_double)]
+                ("Omega_host", _up), ("ldo", C.c_int64), ("lambda_", C.c_double), ("mem_kind", C.c_int32),
+                ("grid_x", cr_grid), ("grid_y", cr_grid)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -70,7 +78,8 @@ class cr_stats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("pcg_solves", C.c_int64), ("pcg_iters", C.c_int64),
                 ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("phase_ms", C.c_double * 8), ("phase_calls", C.c_int64 * 8),
                 ("learned_solves", C.c_int64), ("learned_fallbacks", C.c_int64), ("learned_off", C.c_int64),
-                ("mixed_handovers", C.c_int64), ("pcg_cluster", C.c_int64 * 2)]
+                ("mixed_handovers", C.c_int64), ("pcg_cluster", C.c_int64 * 2),
+                ("pcg_multigrid", C.c_int64 * 2)]
 
 
 class cr_solve_info(C.Structure):
@@ -108,6 +117,8 @@ SIGNATURES = {
     "cr_get_rank": (C.c_int, [C.c_void_p, _ip]),
     "cr_get_factors": (C.c_int, [C.c_void_p, _dp, C.c_int64, _dp, C.c_int64, _dp, C.c_int64]),
     "cr_set_factors": (C.c_int, [C.c_void_p, C.c_int32, _dp, C.c_int64, _dp, C.c_int64, _dp, C.c_int64]),
+    "cr_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]),
+    "cr_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "cr_apply_residual": (C.c_int, [C.c_void_p, C.c_int32, _dp, _dp]),
     "cr_solve_u": (C.c_int, [C.c_void_p, _dp, _dp, _dp, _ip]),
     "cr_solve_v": (C.c_int, [C.c_void_p, _dp, _dp, _dp, _ip]),
@@ -215,7 +226,12 @@ def default_options(**kw) -> cr_options:
 class ConReg:
     """One problem instance on the current CUDA device (see ``include/conreg.h``)."""
 
-    def __init__(self, Lx, Ly, X, Y, Omega, lam: float, stream=None, use_torch_allocator: bool = True, **opts):
+    def __init__(self, Lx, Ly, X, Y, Omega, lam: float, stream=None, use_torch_allocator: bool = True,
+                 device_inputs: bool = False, grids=None, **opts):
+        """``device_inputs``: hand the library device copies of every array
+        (mem_kind = CR_MEM_DEVICE) instead of host pointers.  ``grids``: optional
+        (mask_x, mask_y) voxel boxes (C-order masks, rows numbered in that order)
+        passed at creation."""
         import torch
 
         if not torch.cuda.is_available():
@@ -240,6 +256,42 @@ class ConReg:
         d.Y_host, d.ldy = _ptr(self.Y), self.ny
         d.Omega_host, d.ldo = _ptr(self.Om, _up), self.ny
         d.lambda_ = float(lam)
+        if grids is not None:
+            for name, mask in (("grid_x", grids[0]), ("grid_y", grids[1])):
+                if mask is None:
+                    continue
+                dims = list(mask.shape) + [1] * (3 - mask.ndim)
+                idx = np.ascontiguousarray(np.flatnonzero(np.asarray(mask).ravel()), dtype=np.int32)
+                self._keep.append(idx)
+                g = getattr(d, name)
+                g.dims[:] = dims
+                g.box_index = _ptr(idx, _ip)
+        if device_inputs:
+            # device copies of every array, the descriptor pointing at them
+            dev = torch.device("cuda", torch.cuda.current_device())
+
+            def on_dev(a):
+                t = torch.from_numpy(np.array(a, copy=True, order="F").ravel(order="F")).to(dev)
+                self._keep.append(t)
+                return t.data_ptr()
+
+            for name in ("Lx", "Ly"):
+                c = getattr(d, name)
+                L = Lx if name == "Lx" else Ly
+                setattr(d, name, cr_csr(L.n, C.cast(C.c_void_p(on_dev(np.asarray(L.rowptr, np.int32))), _ip),
+                                        C.cast(C.c_void_p(on_dev(np.asarray(L.col, np.int32))), _ip),
+                                        C.cast(C.c_void_p(on_dev(np.asarray(L.val, np.float64))), _dp)))
+            d.X_host = C.cast(C.c_void_p(on_dev(self.X)), _dp)
+            d.Y_host = C.cast(C.c_void_p(on_dev(self.Y)), _dp)
+            d.Omega_host = C.cast(C.c_void_p(on_dev(self.Om)), _up)
+            for name in ("grid_x", "grid_y"):
+                g = getattr(d, name)
+                if g.box_index:
+                    n = self.nx if name == "grid_x" else self.ny
+                    host = np.ctypeslib.as_array(g.box_index, shape=(n,)).copy()
+                    g.box_index = C.cast(C.c_void_p(on_dev(host)), _ip)
+            d.mem_kind = CR_MEM_DEVICE
+            torch.cuda.synchronize()
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -382,6 +434,18 @@ class ConReg:
         g.h = C.c_void_p(handle)
         return g
 
+    def cr_get_state(self) -> bytes:
+        """Opaque checkpoint of the iterate (rank, U, Z, V, the previous Z)."""
+        n = C.c_size_t(0)
+        _check(self._lib.cr_get_state(self.h, None, C.byref(n)), self.h, "cr_get_state")
+        buf = C.create_string_buffer(n.value)
+        _check(self._lib.cr_get_state(self.h, buf, C.byref(n)), self.h, "cr_get_state")
+        return buf.raw[:n.value]
+
+    def cr_set_state(self, state: bytes):
+        buf = C.create_string_buffer(bytes(state), len(state))
+        _check(self._lib.cr_set_state(self.h, buf, len(state)), self.h, "cr_set_state")
+
     def cr_set_factors(self, U, Z, V):
         U, Z, V = _f64(U), _f64(Z), _f64(V)
         j = Z.shape[0]
@@ -427,7 +491,8 @@ class ConReg:
                 "phase_calls": {PHASES[i]: s.phase_calls[i] for i in range(8)},
                 "learned_solves": s.learned_solves, "learned_fallbacks": s.learned_fallbacks,
                 "learned_off": s.learned_off, "mixed_handovers": s.mixed_handovers,
-                "pcg_cluster": [s.pcg_cluster[0], s.pcg_cluster[1]]}
+                "pcg_cluster": [s.pcg_cluster[0], s.pcg_cluster[1]],
+                "pcg_multigrid": [s.pcg_multigrid[0], s.pcg_multigrid[1]]}
 
     def cr_solve_u(self, v, rhs, allow_notconv: bool = False):
         """(solution, iterations); with ``allow_notconv`` a solve that stopped at

@@ -33,6 +33,7 @@
 #include "conreg.h"
 #include "cr_common.cuh"
 #include "cr_host_linalg.h"
+#include "cr_mg_host.h"
 
 using cr_host::jacobi_svd;
 using cr_host::sym_eig;
@@ -62,6 +63,103 @@ struct HostScal {
 namespace cr {
 // Error text reported by cr_last_error(NULL) for calls without a problem handle.
 void set_global_error(const std::string& msg) { g_create_err = msg; }
+
+// A descriptor whose arrays are device memory (mem_kind = CR_MEM_DEVICE),
+// staged into host vectors: *view points into *store with mem_kind = host.  A
+// host descriptor is passed through unchanged.
+cr_status stage_desc(const cr_problem_desc* d, DescCopy* store, cr_problem_desc* view, std::string& err) {
+  *view = *d;
+  if (d->mem_kind == CR_MEM_HOST) return CR_OK;
+  if (d->mem_kind != CR_MEM_DEVICE) {
+    err = "mem_kind must be CR_MEM_HOST or CR_MEM_DEVICE";
+    return CR_EINVAL;
+  }
+  const int64_t nx = d->nx, ny = d->ny, m = d->ninj;
+  if (nx <= 0 || ny <= 0 || m <= 0 || nx > (1 << 24) || ny > (1 << 24) || m > 4096 || d->ldx < nx || d->ldy < ny ||
+      d->ldo < ny || d->Lx.n != nx || d->Ly.n != ny) {
+    err = "bad sizes";
+    return CR_EINVAL;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    err = "no current CUDA device";
+    return CR_ECUDA;
+  }
+  auto on_device = [&](const void* ptr) {
+    if (!ptr) return false;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
+  };
+  const void* ptrs[] = {d->Lx.rowptr, d->Lx.col, d->Lx.val, d->Ly.rowptr, d->Ly.col, d->Ly.val,
+                        d->X_host,    d->Y_host, d->Omega_host};
+  for (const void* q : ptrs)
+    if (!on_device(q)) {
+      err = "mem_kind = CR_MEM_DEVICE but an array is not device memory of the current GPU";
+      return CR_EINVAL;
+    }
+  auto get = [&](void* dst, const void* src, size_t bytes) {
+    return bytes == 0 || cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost) == cudaSuccess;
+  };
+  bool ok = true;
+  for (int side = 0; side < 2 && ok; ++side) {
+    const cr_csr& c = side == 0 ? d->Lx : d->Ly;
+    std::vector<int32_t>& rp = side == 0 ? store->lx_rp : store->ly_rp;
+    std::vector<int32_t>& col = side == 0 ? store->lx_col : store->ly_col;
+    std::vector<double>& val = side == 0 ? store->lx_val : store->ly_val;
+    rp.resize((size_t)c.n + 1);
+    ok = get(rp.data(), c.rowptr, sizeof(int32_t) * rp.size());
+    if (ok && (rp[0] != 0 || rp[c.n] < 0 || rp[c.n] > (int32_t)((c.n) * 17))) {
+      err = "bad CSR row pointers";
+      return CR_EINVAL;
+    }
+    if (ok) {
+      col.resize((size_t)rp[c.n]);
+      val.resize((size_t)rp[c.n]);
+      ok = get(col.data(), c.col, sizeof(int32_t) * col.size()) && get(val.data(), c.val, sizeof(double) * val.size());
+    }
+    cr_csr& vc = side == 0 ? view->Lx : view->Ly;
+    vc.rowptr = rp.data();
+    vc.col = col.data();
+    vc.val = val.data();
+  }
+  store->X.resize((size_t)nx * m);
+  store->Y.resize((size_t)ny * m);
+  store->Om.resize((size_t)ny * m);
+  ok = ok && cudaMemcpy2D(store->X.data(), nx * sizeof(double), d->X_host, d->ldx * sizeof(double), nx * sizeof(double),
+                          m, cudaMemcpyDeviceToHost) == cudaSuccess;
+  ok = ok && cudaMemcpy2D(store->Y.data(), ny * sizeof(double), d->Y_host, d->ldy * sizeof(double), ny * sizeof(double),
+                          m, cudaMemcpyDeviceToHost) == cudaSuccess;
+  ok = ok && cudaMemcpy2D(store->Om.data(), ny, d->Omega_host, d->ldo, ny, m, cudaMemcpyDeviceToHost) == cudaSuccess;
+  for (int side = 0; side < 2 && ok; ++side) {
+    const cr_grid& g = side == 0 ? d->grid_x : d->grid_y;
+    if (!g.box_index) continue;
+    if (!on_device(g.box_index)) {
+      err = "mem_kind = CR_MEM_DEVICE but a grid's box indices are not device memory of the current GPU";
+      return CR_EINVAL;
+    }
+    std::vector<int32_t>& b = side == 0 ? store->gx : store->gy;
+    b.resize((size_t)(side == 0 ? nx : ny));
+    ok = get(b.data(), g.box_index, sizeof(int32_t) * b.size());
+    (side == 0 ? view->grid_x : view->grid_y).box_index = b.data();
+  }
+  if (!ok) {
+    err = std::string("staging device inputs failed: ") + cudaGetErrorString(cudaGetLastError());
+    return CR_ECUDA;
+  }
+  view->X_host = store->X.data();
+  view->ldx = nx;
+  view->Y_host = store->Y.data();
+  view->ldy = ny;
+  view->Omega_host = store->Om.data();
+  view->ldo = ny;
+  view->mem_kind = CR_MEM_HOST;
+  return CR_OK;
+}
 }  // namespace cr
 
 struct cr_problem;
@@ -79,6 +177,7 @@ struct cr_problem {
   int j = 0;
   std::vector<std::pair<void*, size_t>> allocs;
   DevLap Lx, Ly;
+  DevMg mg[2];  // multigrid hierarchies of L_y (side 0) and L_x (side 1)
   int *xc_ptr = nullptr, *xc_row = nullptr;
   double* xc_val = nullptr;
   DevXLocal xl;
@@ -272,6 +371,24 @@ cr_status readback(cr_problem* p, int lo, int cnt, bool stats) {
 }
 
 // --------------------------------------------------------------------------- set-up helpers
+// Box indices of one side: distinct and inside the D x H x W box.
+bool grid_ok(const int32_t* dims, const int32_t* idx, int64_t n, std::string& err) {
+  if (dims[0] < 1 || dims[1] < 1 || dims[2] < 1 || (int64_t)dims[0] * dims[1] * dims[2] > (1ll << 26)) {
+    err = "bad box dimensions";
+    return false;
+  }
+  const int64_t V = (int64_t)dims[0] * dims[1] * dims[2];
+  std::vector<uint8_t> seen((size_t)V, 0);
+  for (int64_t i = 0; i < n; ++i) {
+    if (idx[i] < 0 || idx[i] >= V || seen[idx[i]]) {
+      err = "box indices out of range or repeated";
+      return false;
+    }
+    seen[idx[i]] = 1;
+  }
+  return true;
+}
+
 struct HostCSR {
   int64_t n;
   std::vector<int32_t> rp, col;
@@ -416,6 +533,147 @@ cr_status build_lap(cr_problem* p, const cr_csr& c, DevLap& L) {
   L.chunk = chunk;
   L.csize = cs;
   if (cs > 0) CUCHK(p, pcg_prepare(0, cs, pcg_smem_bytes(chunk, p->m)));
+  return CR_OK;
+}
+
+// Multigrid hierarchy of one Laplacian (cr_mg_host.h) on the cluster partition
+// of L: level 0 in L's chunks, larger coarse levels in equal chunks over the
+// cluster, levels of at most kMgTailRows rows and the coarsest (at most
+// kMgCoarseMax rows, through the eigenbasis of its pencil) on CTA 0.  Leaves
+// g.nlev = 0 when the hierarchy or its shared memory does not fit.
+cr_status build_mg(cr_problem* p, const cr_csr& c, const DevLap& L, DevMg& g) {
+  g = DevMg{};
+  const int n = (int)c.n;
+  const int C = L.csize;
+  if (C < 1 || n <= kMgCoarseMax) return CR_OK;
+  cr_mg::Csr A;
+  A.rows = A.cols = n;
+  A.rp.assign(n + 1, 0);
+  std::vector<std::pair<int, double>> row;
+  for (int i = 0; i < n; ++i) {
+    row.clear();
+    for (int32_t q = c.rowptr[i]; q < c.rowptr[i + 1]; ++q) row.push_back({c.col[q], c.val[q]});
+    std::sort(row.begin(), row.end());
+    for (size_t k = 0; k < row.size(); ++k) {
+      if (!A.ci.empty() && (int)A.ci.size() > A.rp[i] && A.ci.back() == row[k].first)
+        A.v.back() += row[k].second;
+      else {
+        A.ci.push_back(row[k].first);
+        A.v.push_back(row[k].second);
+      }
+    }
+    A.rp[i + 1] = (int)A.ci.size();
+  }
+  const cr_mg::Hierarchy H = cr_mg::build(A, kMgCoarseMax, kMgMaxLev);
+  const int nlev = (int)H.lev.size();
+  if (nlev < 2 || H.lev.back().L.rows > kMgCoarseMax) return CR_OK;
+  std::vector<double> Q, mu;
+  if (!cr_mg::pencil_basis(H.lev.back().L, H.lev.back().M, Q, mu)) return CR_OK;
+  DevMg h{};
+  h.nlev = nlev;
+  h.nc = H.lev.back().L.rows;
+  h.ld = nlev - 1;
+  int off = 0;
+  for (int l = 0; l < nlev; ++l) {
+    DevMgLevel& V = h.lev[l];
+    V.n = H.lev[l].L.rows;
+    if (l == 0) {
+      V.dist = 1;
+      V.chunk = L.chunk;
+    } else {
+      V.dist = (l < nlev - 1 && V.n > kMgTailRows && C > 1) ? 1 : 0;
+      V.chunk = V.dist ? (V.n + C - 1) / C : V.n;
+      V.off = off;
+      off += 5 * V.chunk;
+    }
+  }
+  for (int l = 1; l < nlev; ++l)
+    if (!h.lev[l].dist) {
+      h.ld = l;
+      break;
+    }
+  h.lvl_elems = off;
+  auto pack = [&](int l, int row) -> int {
+    const DevMgLevel& V = h.lev[l];
+    if (!V.dist) return row;
+    return ((row / V.chunk) << 24) | (row % V.chunk);
+  };
+  for (int l = 0; l < nlev; ++l) {
+    DevMgLevel& V = h.lev[l];
+    const cr_mg::Level& HL = H.lev[l];
+    if (l >= 1) {
+      // L_l + sigma M_l on the union of both patterns (the coarsest level's too, though
+      // its solve goes through the eigenbasis: every level's arrays exist)
+      std::vector<int> rp(V.n + 1, 0), cp;
+      std::vector<double> lv, mv, dl(V.n, 0.0), dm(V.n, 0.0);
+      for (int i = 0; i < V.n; ++i) {
+        int a = HL.L.rp[i], b = HL.M.rp[i];
+        const int ae = HL.L.rp[i + 1], be = HL.M.rp[i + 1];
+        while (a < ae || b < be) {
+          const int ca = a < ae ? HL.L.ci[a] : INT32_MAX, cb = b < be ? HL.M.ci[b] : INT32_MAX;
+          const int col = std::min(ca, cb);
+          const double x = ca == col ? HL.L.v[a++] : 0.0;
+          const double y = cb == col ? HL.M.v[b++] : 0.0;
+          cp.push_back(pack(l, col));
+          lv.push_back(x);
+          mv.push_back(y);
+          if (col == i) {
+            dl[i] = x;
+            dm[i] = y;
+          }
+        }
+        rp[i + 1] = (int)cp.size();
+      }
+      int *drp = nullptr, *dcp = nullptr;
+      double *dlv = nullptr, *dmv = nullptr, *ddl = nullptr, *ddm = nullptr;
+      TRY(upload(p, &drp, rp));
+      TRY(upload(p, &dcp, cp));
+      TRY(upload(p, &dlv, lv));
+      TRY(upload(p, &dmv, mv));
+      TRY(upload(p, &ddl, dl));
+      TRY(upload(p, &ddm, dm));
+      V.rp = drp;
+      V.cp = dcp;
+      V.lv = dlv;
+      V.mv = dmv;
+      V.dl = ddl;
+      V.dm = ddm;
+    }
+    if (l < nlev - 1) {
+      std::vector<int> prp(HL.P.rp), pcp(HL.P.ci.size()), rrp(HL.R.rp), rcp(HL.R.ci.size());
+      for (size_t q = 0; q < HL.P.ci.size(); ++q) pcp[q] = pack(l + 1, HL.P.ci[q]);
+      for (size_t q = 0; q < HL.R.ci.size(); ++q) rcp[q] = pack(l, HL.R.ci[q]);
+      int *d1 = nullptr, *d2 = nullptr, *d3 = nullptr, *d4 = nullptr;
+      double *d5 = nullptr, *d6 = nullptr;
+      TRY(upload(p, &d1, prp));
+      TRY(upload(p, &d2, pcp));
+      TRY(upload(p, &d5, HL.P.v));
+      TRY(upload(p, &d3, rrp));
+      TRY(upload(p, &d4, rcp));
+      TRY(upload(p, &d6, HL.R.v));
+      V.prp = d1;
+      V.pcp = d2;
+      V.pv = d5;
+      V.rrp = d3;
+      V.rcp = d4;
+      V.rv = d6;
+    }
+  }
+  double *dQ = nullptr, *dmu = nullptr;
+  TRY(upload(p, &dQ, Q));
+  TRY(upload(p, &dmu, mu));
+  h.cQ = dQ;
+  h.cmu = dmu;
+  const size_t cap = 227 * 1024;
+  for (int f = 0; f < 2; ++f) {
+    const size_t b = mg_smem_bytes(h, L.chunk, p->m, f == 0);
+    h.smem[f] = b <= cap ? b : 0;
+  }
+  if (h.smem[0] == 0 && h.smem[1] == 0) return CR_OK;
+  CUCHK(p, mg_prepare());
+  for (int f = 0; f < 2; ++f)
+    if (h.smem[f] && !mg_cluster_ok(C, h.smem[f], f == 0)) h.smem[f] = 0;
+  g = h;
   return CR_OK;
 }
 
@@ -623,7 +881,18 @@ bool use_grid_pcg(const cr_problem* p, int side, bool fp32) {
 // One Jacobi-PCG solve on the cluster-resident kernel, or on the grid-wide
 // kernel (use_grid_pcg; that path waits for the result, to turn a grid
 // barrier timeout into CR_ETIMEOUT).
+bool use_mg(const cr_problem* p, int side, bool fp32) {
+  const DevMg& g = p->mg[side];
+  return p->opt.precond == CR_PRECOND_MULTIGRID && g.nlev >= 2 && g.smem[fp32 ? 0 : 1] > 0;
+}
+
 cr_status run_pcg(cr_problem* p, int side, const double* b, double* x, int maxit, double tol, bool fp32) {
+  if (use_mg(p, side, fp32)) {
+    prof_begin(p, CR_PHASE_PCG_KERNEL);
+    CUCHK(p, mg_pcg_launch(pcg_args(p, side, b, x, maxit, tol, fp32), p->mg[side], side, p->st));
+    prof_end(p, CR_PHASE_PCG_KERNEL);
+    return CR_OK;
+  }
   if (!use_grid_pcg(p, side, fp32)) {
     prof_begin(p, CR_PHASE_PCG_KERNEL);
     CUCHK(p, pcg_launch(pcg_args(p, side, b, x, maxit, tol, fp32), side, p->st));
@@ -1275,14 +1544,25 @@ void cr_destroy(cr_problem* p) {
   delete p;
 }
 
-cr_status cr_create(const cr_problem_desc* d, const cr_options* o, cr_problem** out) {
+cr_status cr_create(const cr_problem_desc* d_in, const cr_options* o, cr_problem** out) {
   if (out) *out = nullptr;
   g_create_err.clear();
   auto bad = [](const std::string& m) {
     g_create_err = m;
     return CR_EINVAL;
   };
-  if (!d || !out) return bad("null argument");
+  if (!d_in || !out) return bad("null argument");
+  DescCopy staged;
+  cr_problem_desc dview;
+  {
+    std::string serr;
+    const cr_status ss = stage_desc(d_in, &staged, &dview, serr);
+    if (ss != CR_OK) {
+      g_create_err = serr;
+      return ss;
+    }
+  }
+  const cr_problem_desc* d = &dview;
   cr_options opt;
   cr_options_default(&opt);
   if (o) {
@@ -1300,6 +1580,8 @@ cr_status cr_create(const cr_problem_desc* d, const cr_options* o, cr_problem** 
   if (opt.alloc && !opt.free) return bad("alloc given without free");
   std::string err;
   if (check_csr(d->Lx, nx, "Lx", err) != CR_OK || check_csr(d->Ly, ny, "Ly", err) != CR_OK) return bad(err);
+  if (d->grid_x.box_index && !grid_ok(d->grid_x.dims, d->grid_x.box_index, nx, err)) return bad("grid_x: " + err);
+  if (d->grid_y.box_index && !grid_ok(d->grid_y.dims, d->grid_y.box_index, ny, err)) return bad("grid_y: " + err);
   for (int64_t a = 0; a < m; ++a) {
     for (int64_t i = 0; i < nx; ++i)
       if (!std::isfinite(d->X_host[i + a * d->ldx])) return bad("X has a non-finite entry");
@@ -1342,6 +1624,10 @@ cr_status cr_create(const cr_problem_desc* d, const cr_options* o, cr_problem** 
   } while (0)
   CK(build_lap(p, d->Ly, p->Ly));
   CK(build_lap(p, d->Lx, p->Lx));
+  if (opt.precond == CR_PRECOND_MULTIGRID) {
+    CK(build_mg(p, d->Ly, p->Ly, p->mg[0]));
+    CK(build_mg(p, d->Lx, p->Lx, p->mg[1]));
+  }
   // X: CSC, CSR by rows, and per-CTA local CSC on the x partition
   {
     std::vector<int> cp(m + 1, 0), row;
@@ -1395,6 +1681,15 @@ cr_status cr_create(const cr_problem_desc* d, const cr_options* o, cr_problem** 
     CK(upload(p, &d_lvf, lvf));
     CK(upload(p, &d_rvf, rvf));
     p->xl = DevXLocal{d_lp, d_lr, d_lv, d_rp, d_rc, d_rv, d_lvf, d_rvf};
+    if (p->mg[1].nlev > 0) {
+      // |X_a|^2: the v side's mean data weight enters the multigrid shift
+      std::vector<double> xn2(m, 0.0);
+      for (int64_t a = 0; a < m; ++a)
+        for (int q = cp[a]; q < cp[a + 1]; ++q) xn2[a] += val[q] * val[q];
+      double* dx = nullptr;
+      CK(upload(p, &dx, xn2));
+      p->mg[1].xn2 = dx;
+    }
   }
   // Omega o Y, Omega; norms |D|_F (via the m x m Gram products, all terms of
   // one sign pattern: |D|^2 = tr((OmY^T OmY)(X^T X))) and |Omega o Y|^2
@@ -1533,6 +1828,8 @@ cr_status cr_create(const cr_problem_desc* d, const cr_options* o, cr_problem** 
   }
   refresh_E(p);
   if ((s = sync(p)) != CR_OK) return abort_create(s);
+  if (d->grid_y.box_index) CK(cr_set_voxel_grid(p, 0, d->grid_y.dims, d->grid_y.box_index));
+  if (d->grid_x.box_index) CK(cr_set_voxel_grid(p, 1, d->grid_x.dims, d->grid_x.box_index));
 #undef CK
   *out = p;
   return CR_OK;
@@ -1583,14 +1880,9 @@ cr_status cr_residual(cr_problem* p, double* relres, double* J, double* dW) {
 cr_status cr_set_voxel_grid(cr_problem* p, int32_t side, const int32_t* dims, const int32_t* box_index) {
   if (!p || (side != 0 && side != 1) || !dims || !box_index) return CR_EINVAL;
   const int n = side == 0 ? p->ny : p->nx;
-  const int64_t V = (int64_t)dims[0] * dims[1] * dims[2];
-  if (dims[0] < 1 || dims[1] < 1 || dims[2] < 1 || V > (1ll << 26)) return fail(p, CR_EINVAL, "bad box dimensions");
+  std::string err;
+  if (!grid_ok(dims, box_index, n, err)) return fail(p, CR_EINVAL, err);
   std::vector<int> idx(box_index, box_index + n);
-  std::vector<uint8_t> seen((size_t)V, 0);
-  for (int i = 0; i < n; ++i) {
-    if (idx[i] < 0 || idx[i] >= V || seen[idx[i]]) return fail(p, CR_EINVAL, "box indices out of range or repeated");
-    seen[idx[i]] = 1;
-  }
   int* d = nullptr;
   TRY(upload(p, &d, idx));
   p->box[side] = d;
@@ -1661,7 +1953,9 @@ cr_status cr_get_stats(cr_problem* p, cr_stats* s, int32_t reset) {
   s->mixed_handovers = p->mixed_handovers;
   for (int side = 0; side < 2; ++side) {
     const DevLap& L = side == 0 ? p->Ly : p->Lx;
-    s->pcg_cluster[side] = use_grid_pcg(p, side, p->opt.precision == CR_MIXED) ? 0 : L.csize;
+    const bool f32 = p->opt.precision == CR_MIXED;
+    s->pcg_cluster[side] = (use_mg(p, side, f32) || !use_grid_pcg(p, side, f32)) ? L.csize : 0;
+    s->pcg_multigrid[side] = use_mg(p, side, f32) ? p->mg[side].nlev : 0;
   }
   for (int i = 0; i < CR_NPHASE; ++i) {
     s->phase_ms[i] = p->phase_ms[i];
@@ -1753,6 +2047,100 @@ cr_status cr_get_factors(cr_problem* p, double* U, int64_t ldu, double* Zh, int6
   if (Zh)
     CUCHK(p, cudaMemcpy2DAsync(Zh, ldz * sizeof(double), p->Z, (size_t)p->rcap * sizeof(double), j * sizeof(double),
                                j, cudaMemcpyDeviceToHost, p->st));
+  return sync(p);
+}
+
+namespace {
+// Checkpoint layout: StateHeader, then U (ny x j), Z (j x j), Z of the step before (j x j), V (nx x j),
+// float64 column-major, contiguous.
+struct StateHeader {
+  char magic[8];
+  int64_t ny, nx, m, j;
+  double lam;
+  uint64_t checksum;  // FNV-1a of the payload bytes
+};
+constexpr char kStateMagic[8] = {'C', 'R', 'S', 'T', 'A', 'T', 'E', '1'};
+
+uint64_t fnv1a(const unsigned char* b, size_t n) {
+  uint64_t h = 1469598103934665603ull;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= b[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+size_t state_bytes(int64_t ny, int64_t nx, int64_t j) {
+  return sizeof(StateHeader) + sizeof(double) * (size_t)(ny * j + 2 * j * j + nx * j);
+}
+}  // namespace
+
+cr_status cr_get_state(cr_problem* p, void* buf, size_t* bytes) {
+  if (!p || !bytes) return CR_EINVAL;
+  const int j = p->j;
+  const size_t need = state_bytes(p->ny, p->nx, j);
+  if (!buf) {
+    *bytes = need;
+    return CR_OK;
+  }
+  if (*bytes < need) {
+    *bytes = need;
+    return fail(p, CR_EINVAL, "state buffer too small (" + std::to_string(need) + " bytes needed)");
+  }
+  StateHeader h{};
+  std::memcpy(h.magic, kStateMagic, 8);
+  h.ny = p->ny;
+  h.nx = p->nx;
+  h.m = p->m;
+  h.j = j;
+  h.lam = p->lam;
+  unsigned char* out = static_cast<unsigned char*>(buf);
+  double* U = reinterpret_cast<double*>(out + sizeof(StateHeader));
+  double* Z = U + (size_t)p->ny * j;
+  double* Zp = Z + (size_t)j * j;
+  double* V = Zp + (size_t)j * j;
+  if (j > 0) {
+    TRY(cr_get_factors(p, U, p->ny, Z, j, V, p->nx));
+    CUCHK(p, cudaMemcpy2DAsync(Zp, j * sizeof(double), p->Zprev, (size_t)p->rcap * sizeof(double), j * sizeof(double),
+                               j, cudaMemcpyDeviceToHost, p->st));
+    p->d2h_bytes += (int64_t)sizeof(double) * j * j;
+    TRY(sync(p));
+  }
+  h.checksum = fnv1a(out + sizeof(StateHeader), need - sizeof(StateHeader));
+  std::memcpy(out, &h, sizeof(h));
+  *bytes = need;
+  return CR_OK;
+}
+
+cr_status cr_set_state(cr_problem* p, const void* buf, size_t bytes) {
+  if (!p || !buf) return CR_EINVAL;
+  if (bytes < sizeof(StateHeader)) return fail(p, CR_EINVAL, "state buffer shorter than its header");
+  StateHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  if (std::memcmp(h.magic, kStateMagic, 8) != 0) return fail(p, CR_EINVAL, "not a cr_get_state buffer");
+  if (h.ny != p->ny || h.nx != p->nx || h.m != p->m || std::memcmp(&h.lam, &p->lam, sizeof(double)) != 0)
+    return fail(p, CR_EINVAL, "state belongs to a problem with other sizes or another lambda");
+  if (h.j < 0 || h.j > (int64_t)std::min(p->ny, p->nx)) return fail(p, CR_EINVAL, "corrupt state (rank)");
+  if (h.j > p->rcap) return fail(p, CR_ESTATE, "state rank exceeds r_cap");
+  const int j = (int)h.j;
+  const size_t need = state_bytes(p->ny, p->nx, j);
+  if (bytes < need) return fail(p, CR_EINVAL, "state buffer truncated");
+  const unsigned char* in = static_cast<const unsigned char*>(buf);
+  if (fnv1a(in + sizeof(StateHeader), need - sizeof(StateHeader)) != h.checksum)
+    return fail(p, CR_EINVAL, "state checksum mismatch (corrupt buffer)");
+  // the payload may sit at any alignment in the caller's buffer
+  std::vector<double> pay((need - sizeof(StateHeader)) / sizeof(double));
+  std::memcpy(pay.data(), in + sizeof(StateHeader), need - sizeof(StateHeader));
+  const double* U = pay.data();
+  const double* Z = U + (size_t)p->ny * j;
+  const double* Zp = Z + (size_t)j * j;
+  const double* V = Zp + (size_t)j * j;
+  TRY(cr_set_factors(p, j, j ? U : nullptr, p->ny, j ? Z : nullptr, std::max(j, 1), j ? V : nullptr, p->nx));
+  if (j > 0) {
+    CUCHK(p, cudaMemcpy2DAsync(p->Zprev, (size_t)p->rcap * sizeof(double), Zp, j * sizeof(double), j * sizeof(double),
+                               j, cudaMemcpyHostToDevice, p->st));
+    p->h2d_bytes += (int64_t)sizeof(double) * j * j;
+  }
   return sync(p);
 }
 

@@ -61,13 +61,26 @@ bool cols_ok(const int32_t* c, int32_t n, int64_t m) {
 
 }  // namespace
 
-extern "C" cr_status cr_solve_batch(const cr_problem_desc* desc, const cr_options* opts, const cr_member* members,
-                                    int32_t n_members, int32_t r_max, double tau, double relres_target,
-                                    int32_t concurrency, cr_member_result* results, cr_problem** keep) {
-  if (!desc || !members || !results || n_members < 0 || r_max < 0 || !(tau >= 0.0)) {
+extern "C" cr_status cr_solve_batch(const cr_problem_desc* desc_in, const cr_options* opts,
+                                    const cr_member* members, int32_t n_members, int32_t r_max, double tau,
+                                    double relres_target, int32_t concurrency, cr_member_result* results,
+                                    cr_problem** keep) {
+  if (!desc_in || !members || !results || n_members < 0 || r_max < 0 || !(tau >= 0.0)) {
     cr::set_global_error("cr_solve_batch: bad arguments");
     return CR_EINVAL;
   }
+  // device inputs are staged once; every member gathers its columns from the host copy
+  cr::DescCopy staged;
+  cr_problem_desc dview;
+  {
+    std::string err;
+    const cr_status ss = cr::stage_desc(desc_in, &staged, &dview, err);
+    if (ss != CR_OK) {
+      cr::set_global_error("cr_solve_batch: " + err);
+      return ss;
+    }
+  }
+  const cr_problem_desc* desc = &dview;
   for (int32_t k = 0; k < n_members; ++k) {
     const cr_member& mb = members[k];
     if (mb.n_fit < 1 || mb.n_test < 0 || !cols_ok(mb.fit_cols, mb.n_fit, desc->ninj) ||

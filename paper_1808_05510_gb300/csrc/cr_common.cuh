@@ -16,7 +16,24 @@
 
 #include <atomic>
 
+#include <string>
+#include <vector>
+
+#include "conreg.h"
+
 struct cr_net;
+
+namespace cr {
+
+// Host copies of a descriptor's device arrays (cr_problem_desc.mem_kind = CR_MEM_DEVICE).
+struct DescCopy {
+  std::vector<int32_t> lx_rp, lx_col, ly_rp, ly_col, gx, gy;
+  std::vector<double> lx_val, ly_val, X, Y;
+  std::vector<uint8_t> Om;
+};
+// Stage a device descriptor into *store (host view in *view); host descriptors pass through.
+cr_status stage_desc(const cr_problem_desc* d, DescCopy* store, cr_problem_desc* view, std::string& err);
+}  // namespace cr
 
 namespace cr {
 
@@ -96,6 +113,63 @@ struct PcgArgs {
   int force_generic;       // 1: always use the shared/global-memory kernel
   int fp32;                // 1: float32 vectors and arithmetic, float64 inner products and scalars
 };
+
+// ---------------------------------------------------------------- cr_mg.cu
+// Multigrid preconditioner of the ALS sub-problems: the hierarchy of one
+// Laplacian (built on the host by cr_mg_host.h) in device memory.  Level 0 is
+// the fine grid itself (DevLap, partitioned in chunks of L.chunk rows over the
+// cluster); levels l >= 1 keep L_l and M_l entry by entry so that the kernel
+// forms L_l + sigma M_l for any shift.  Column references are packed as
+// (owner CTA << 24) | local row in the owner's partition of the referenced level.
+constexpr int kMgMaxLev = 8;
+constexpr int kMgCoarseMax = 64;  // rows of the coarsest level (solved through its eigenbasis)
+constexpr int kMgTailRows = 512;  // levels of at most this many rows run on CTA 0 alone
+
+struct DevMgLevel {
+  int n = 0;       // rows
+  int chunk = 0;   // rows per CTA when distributed; n when on CTA 0 alone
+  int dist = 0;    // 1: distributed over the cluster, 0: CTA 0 alone
+  int off = 0;     // offset of the level's five work vectors in the kernel's shared memory (elements)
+  // operator rows (levels >= 1): CSR by global row, packed column refs, values of L_l and M_l
+  const int* rp = nullptr;
+  const int* cp = nullptr;
+  const double* lv = nullptr;
+  const double* mv = nullptr;
+  const double* dl = nullptr;  // diagonals of L_l and M_l
+  const double* dm = nullptr;
+  // prolongation from level l+1 (CSR by row of this level, refs into level l+1)
+  const int* prp = nullptr;
+  const int* pcp = nullptr;
+  const double* pv = nullptr;
+  // restriction into level l+1 (CSR by row of level l+1, refs into this level)
+  const int* rrp = nullptr;
+  const int* rcp = nullptr;
+  const double* rv = nullptr;
+};
+
+struct DevMg {
+  int nlev = 0;                // levels, the last one the coarsest (CTA 0, dense)
+  int ld = 0;                  // first level that runs on CTA 0 alone
+  int nc = 0;                  // rows of the coarsest level
+  DevMgLevel lev[kMgMaxLev];
+  // (L_c + sigma M_c)^-1 = Q diag(1 / (mu + sigma)) Q^T on the coarsest level
+  const double* cQ = nullptr;  // nc x nc, column-major
+  const double* cmu = nullptr; // nc
+  const double* xn2 = nullptr; // v side: |X_a|^2 per injection (mean data weight of the shift)
+  int lvl_elems = 0;           // shared-memory elements of the levels >= 1
+  size_t smem[2] = {0, 0};     // dynamic shared memory of the kernel for T = float, double (0: does not fit)
+};
+
+// Dynamic shared memory of the multigrid PCG for T (bytes), from the level sizes.
+size_t mg_smem_bytes(const DevMg& g, int chunk0, int m, bool fp32);
+// Kernel attributes for the multigrid PCG (cluster size up to 16, large shared memory).
+cudaError_t mg_prepare();
+// Whether a cluster of csize CTAs with smem bytes each fits on this device (after mg_prepare).
+bool mg_cluster_ok(int csize, size_t smem, bool fp32);
+// One PCG solve of the system of `a` (side 0: Eq. ALS_linsys, 1: Eq. ALS_linsys_v)
+// preconditioned by two V-cycles of L + sigma I (scaled by 1 / lam), on the cluster
+// partition of a.L.  a.x is the initial guess and the result; a.p, a.sv, a.omt are work.
+cudaError_t mg_pcg_launch(const PcgArgs& a, const DevMg& g, int side, cudaStream_t st);
 
 // ---------------------------------------------------------------- cr_pcg_grid.cu
 // Grid-wide PCG (vectors in HBM, all SMs) for grids the register-resident cluster kernel does not take.

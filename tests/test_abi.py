@@ -63,7 +63,8 @@ def _desc(p, **over):
     return d, keep
 
 
-@pytest.mark.parametrize("case", ["nan_x", "inf_y", "omega2", "lam0", "lamneg", "nonsym", "badcol", "rcap"])
+@pytest.mark.parametrize("case", ["nan_x", "inf_y", "omega2", "lam0", "lamneg", "nonsym", "badcol", "rcap",
+                                  "mem_kind", "grid_dup", "grid_box"])
 def test_create_rejects_invalid_input(lib, case):
     p = synth.rect2d()
     over = {}
@@ -85,6 +86,15 @@ def test_create_rejects_invalid_input(lib, case):
     elif case == "rcap":
         opts = cr.default_options(r_cap=p.nx + 1)
     d, keep = _desc(p, **over)
+    if case == "mem_kind":
+        d.mem_kind = 7
+    elif case in ("grid_dup", "grid_box"):
+        idx = np.arange(p.ny, dtype=np.int32)
+        if case == "grid_dup":
+            idx[1] = idx[0]  # two rows on one voxel
+        keep.append(idx)
+        d.grid_y.dims[:] = (1, 9, 7) if case == "grid_dup" else (1, 2, 2)  # grid_box: box smaller than the rows
+        d.grid_y.box_index = cr._ptr(idx, cr._ip)
     h = C.c_void_p()
     st = lib.cr_create(C.byref(d), C.byref(opts), C.byref(h))
     assert st == cr.CR_EINVAL
@@ -96,7 +106,7 @@ def test_destroy_null_is_noop(lib):
     lib.cr_destroy(None)
 
 
-STRUCTS = ["cr_csr", "cr_problem_desc", "cr_options", "cr_rank1_info", "cr_proj_info", "cr_stats", "cr_solve_info",
+STRUCTS = ["cr_csr", "cr_grid", "cr_problem_desc", "cr_options", "cr_rank1_info", "cr_proj_info", "cr_stats", "cr_solve_info",
            "cr_member", "cr_member_result", "cr_solution_stats"]
 
 
