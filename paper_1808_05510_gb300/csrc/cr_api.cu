@@ -664,10 +664,83 @@ cr_status build_mg(cr_problem* p, const cr_csr& c, const DevLap& L, DevMg& g) {
   TRY(upload(p, &dmu, mu));
   h.cQ = dQ;
   h.cmu = dmu;
+  // per-CTA tables: byte layout of one CTA's sections (sizes are maxima over the CTAs)
+  auto rows_of = [&](int l, int r) -> int {
+    const DevMgLevel& V = h.lev[l];
+    if (!V.dist) return r == 0 ? V.n : 0;
+    return std::max(0, std::min(V.n - r * V.chunk, V.chunk));
+  };
+  auto beg_of = [&](int l, int r) -> int { return h.lev[l].dist ? r * h.lev[l].chunk : 0; };
+  auto max_entries = [&](int l, const std::vector<int>& rp) -> int64_t {  // rows of level l, CSR rp
+    int64_t mx = 0;
+    for (int r = 0; r < C; ++r) {
+      const int b = beg_of(l, r), nr = rows_of(l, r);
+      if (nr > 0) mx = std::max<int64_t>(mx, rp[b + nr] - rp[b]);
+    }
+    return mx;
+  };
+  int64_t tb = 0;
+  auto sect = [&](int64_t bytes) {
+    const int64_t at = tb;
+    tb += (bytes + 15) / 16 * 16;
+    return at;
+  };
+  const bool unit = L.offw == nullptr;
+  h.nb_a = sect(4 * (int64_t)L.K * L.chunk);
+  h.nb_c = unit ? -1 : sect(8 * (int64_t)L.K * L.chunk);
+  h.dg = sect(8 * (int64_t)L.chunk);
+  for (int l = 0; l < nlev - 1; ++l) {
+    DevMgLevel& V = h.lev[l];
+    const cr_mg::Level& HL = H.lev[l];
+    const int rows = l == 0 ? L.chunk : V.chunk;
+    if (l >= 1) {
+      // the operator rows as uploaded (union of the L and M patterns)
+      std::vector<int> urp(V.n + 1, 0);
+      for (int i = 0; i < V.n; ++i) {
+        int a = HL.L.rp[i], b = HL.M.rp[i], cnt = 0;
+        const int ae = HL.L.rp[i + 1], be = HL.M.rp[i + 1];
+        while (a < ae || b < be) {
+          const int ca = a < ae ? HL.L.ci[a] : INT32_MAX, cb = b < be ? HL.M.ci[b] : INT32_MAX;
+          const int col = std::min(ca, cb);
+          if (ca == col) ++a;
+          if (cb == col) ++b;
+          ++cnt;
+        }
+        urp[i + 1] = urp[i] + cnt;
+      }
+      const int64_t e = max_entries(l, urp);
+      V.op_rp = sect(4 * (int64_t)(rows + 1));
+      V.op_a = sect(4 * e);
+      V.op_c = sect(8 * e);
+    }
+    const int64_t ep = max_entries(l, HL.P.rp);
+    V.p_rp = sect(4 * (int64_t)(rows + 1));
+    V.p_a = sect(4 * ep);
+    V.p_c = sect(8 * ep);
+    const int rows1 = h.lev[l + 1].chunk;
+    const int64_t er = max_entries(l + 1, HL.R.rp);
+    V.r_rp = sect(4 * (int64_t)(rows1 + 1));
+    V.r_a = sect(4 * er);
+    V.r_c = sect(8 * er);
+  }
+  h.tab_bytes = tb;
+  h.smw = (&g == &p->mg[1] && p->m <= kMgSmwMax) ? 1 : 0;  // v side, small enough data term
   const size_t cap = 227 * 1024;
+  bool need_glob = false;
   for (int f = 0; f < 2; ++f) {
-    const size_t b = mg_smem_bytes(h, L.chunk, p->m, f == 0);
-    h.smem[f] = b <= cap ? b : 0;
+    const size_t with = mg_smem_bytes(h, L.chunk, p->m, f == 0, true);
+    const size_t without = mg_smem_bytes(h, L.chunk, p->m, f == 0, false);
+    h.tab_smem[f] = with <= cap ? 1 : 0;
+    h.smem[f] = with <= cap ? with : (without <= cap ? without : 0);
+    if (h.smem[f] && !h.tab_smem[f]) need_glob = true;
+  }
+  if (need_glob) TRY(dalloc(p, &h.tab_glob, (size_t)C * h.tab_bytes));
+  if (h.smw) {
+    // the cache of the v side's Sherman-Morrison-Woodbury correction; smw_sig = {shift, precision}
+    // of the MX it holds (0: none), so a launch of either precision knows whether to rebuild it
+    TRY(dalloc(p, &h.smw_mx, (size_t)n * p->m));
+    TRY(dalloc(p, &h.smw_xx, (size_t)p->m * p->m));
+    TRY(dalloc(p, &h.smw_sig, 3));
   }
   if (h.smem[0] == 0 && h.smem[1] == 0) return CR_OK;
   CUCHK(p, mg_prepare());

@@ -145,6 +145,14 @@ struct DevMgLevel {
   const int* rrp = nullptr;
   const int* rcp = nullptr;
   const double* rv = nullptr;
+  // This level's sections of a CTA's tables (byte offsets from the CTA's table
+  // base): operator rows (levels 1 .. nlev-2), prolongation rows (level l's own
+  // rows), restriction rows (level l+1's own rows).  Each section: a local row
+  // pointer (rows + 1 ints), then the entries' 32-bit cluster addresses, then
+  // their coefficients (8-byte slots).
+  int64_t op_rp = 0, op_a = 0, op_c = 0;
+  int64_t p_rp = 0, p_a = 0, p_c = 0;
+  int64_t r_rp = 0, r_a = 0, r_c = 0;
 };
 
 struct DevMg {
@@ -158,10 +166,30 @@ struct DevMg {
   const double* xn2 = nullptr; // v side: |X_a|^2 per injection (mean data weight of the shift)
   int lvl_elems = 0;           // shared-memory elements of the levels >= 1
   size_t smem[2] = {0, 0};     // dynamic shared memory of the kernel for T = float, double (0: does not fit)
+  // Tables each CTA fills at launch for the rows it owns: the 32-bit
+  // cluster-window address of every referenced entry (relative to its level's
+  // first vector) and its coefficient in the solve's precision.  Level 0's
+  // neighbour addresses (slot-major, K x chunk0; a missing neighbour points at a
+  // zero word) and coefficients (weighted Laplacians only) and its diagonal come
+  // first, then each level's sections.  They live in the CTA's shared memory
+  // when they fit (tab_smem), else in tab_glob + rank * tab_bytes.
+  int64_t nb_a = 0, nb_c = -1, dg = 0;  // byte offsets; nb_c < 0: unit weights (coefficient -1)
+  int64_t tab_bytes = 0;               // bytes of one CTA's tables
+  int tab_smem[2] = {0, 0};            // tables in shared memory for T = float, double
+  char* tab_glob = nullptr;            // csize * tab_bytes bytes when a precision keeps them in global memory
+  // v side, ninj <= kMgSmwMax: Sherman-Morrison-Woodbury correction of the preconditioner for the
+  // rank-ninj data term X diag(s) X^T.  Cached per problem: MX = M0^-1 X (n x ninj, row i at i * ninj,
+  // in the kernel's precision), X^T MX (ninj x ninj, float64) and the shift they were formed with.
+  int smw = 0;
+  double* smw_mx = nullptr;
+  double* smw_xx = nullptr;
+  double* smw_sig = nullptr;  // [0]: the shift MX was formed with (0 = none), [1]: its precision (bytes of T)
 };
+constexpr int kMgSmwMax = 32;
 
-// Dynamic shared memory of the multigrid PCG for T (bytes), from the level sizes.
-size_t mg_smem_bytes(const DevMg& g, int chunk0, int m, bool fp32);
+// Dynamic shared memory of the multigrid PCG for T (bytes), from the level sizes,
+// without (tables = false) or with the CTA's tables.
+size_t mg_smem_bytes(const DevMg& g, int chunk0, int m, bool fp32, bool tables);
 // Kernel attributes for the multigrid PCG (cluster size up to 16, large shared memory).
 cudaError_t mg_prepare();
 // Whether a cluster of csize CTAs with smem bytes each fits on this device (after mg_prepare).
