@@ -62,7 +62,7 @@ def parse(argv=None):
     ap.add_argument("--no-post", action="store_true", help="skip the post-processing measurement")
     ap.add_argument("--batch-r", type=int, default=50, help="rank of every sweep member in the batched form")
     ap.add_argument("--learn-steps", type=int, default=200)
-    ap.add_argument("--precond", default="multigrid", choices=["multigrid", "jacobi"],
+    ap.add_argument("--precond", default="auto", choices=["auto", "multigrid", "jacobi"],
                     help="preconditioner of the ALS sub-solves in the headline forms")
     ap.add_argument("--no-jacobi", action="store_true", help="skip the Jacobi-PCG forms timed beside the headline")
     ap.add_argument("--ttr-r", type=int, default=500, help="rank cap of the visual-cortex time to relres 1e-6")
@@ -244,10 +244,10 @@ def run_ours(args, rank, world, local_rank):
     p, cfg = workload(args, rank)
     stream = torch.cuda.current_stream()
     l2buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    from paper_1808_05510_gb300.conreg import (CR_FP64, CR_MIXED, CR_PRECOND_JACOBI, CR_PRECOND_LEARNED,
-                                               CR_PRECOND_MULTIGRID)
+    from paper_1808_05510_gb300.conreg import (CR_FP64, CR_MIXED, CR_PRECOND_AUTO, CR_PRECOND_JACOBI,
+                                               CR_PRECOND_LEARNED, CR_PRECOND_MULTIGRID)
 
-    head_pc = CR_PRECOND_MULTIGRID if args.precond == "multigrid" else CR_PRECOND_JACOBI
+    head_pc = {"auto": CR_PRECOND_AUTO, "multigrid": CR_PRECOND_MULTIGRID, "jacobi": CR_PRECOND_JACOBI}[args.precond]
 
     def measure(prec, net=None, steps=None, warmup=None, precond=None):
         steps = args.steps if steps is None else steps
@@ -309,7 +309,8 @@ def run_ours(args, rank, world, local_rank):
         achieved = bytes_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
         return {"value": value, "ms_per_step": t_max / steps, "steps": steps, "warmup": warmup,
                 "precond": {CR_PRECOND_JACOBI: "jacobi", CR_PRECOND_LEARNED: "learned (flexible CG, Jacobi judge)",
-                            CR_PRECOND_MULTIGRID: "multigrid"}[pc],
+                            CR_PRECOND_MULTIGRID: "multigrid", CR_PRECOND_AUTO: "auto (multigrid on the v side; "
+                            "u side multigrid in float64 or above 20,000 rows, else Jacobi)"}[pc],
                 "pcg_multigrid_levels": stats["pcg_multigrid"], "time_to_relres_s": ttr,
                 "relres_reached_steps": len(reached), "final_relres": infos[-1]["relres"],
                 "final_rank": infos[-1]["rank"], "stop": infos[-1]["stop_name"],

@@ -54,9 +54,18 @@ typedef enum { CR_FP64 = 0, CR_MIXED = 1 } cr_precision;
 /* Preconditioner of the u/v PCG solves.  CR_PRECOND_MULTIGRID: two V-cycles of
  * smoothed-aggregation multigrid for L + sigma I per application (the inverse
  * of lam (L + sigma I)^2, sigma^2 = the Laplacian shift plus the mean data
- * weight over lam), hierarchy built once from L at cr_create; sizes whose
- * vectors do not fit one thread-block cluster fall back to Jacobi. */
-typedef enum { CR_PRECOND_JACOBI = 0, CR_PRECOND_LEARNED = 1, CR_PRECOND_MULTIGRID = 2 } cr_precond;
+ * weight over lam), hierarchy built once from L at cr_create; on the v side
+ * with at most 32 injections the data term is added exactly by
+ * Sherman-Morrison-Woodbury; sizes whose vectors do not fit one thread-block
+ * cluster fall back to Jacobi.  CR_PRECOND_AUTO: multigrid on the v side; on
+ * the u side multigrid in the float64 form or above 20,000 rows, Jacobi
+ * otherwise (there Jacobi's few cheap float32 iterations are faster). */
+typedef enum {
+  CR_PRECOND_JACOBI = 0,
+  CR_PRECOND_LEARNED = 1,
+  CR_PRECOND_MULTIGRID = 2,
+  CR_PRECOND_AUTO = 3
+} cr_precond;
 typedef enum { CR_STOP_NONE = 0, CR_STOP_RMAX = 1, CR_STOP_DW = 2, CR_STOP_RELRES = 3, CR_STOP_RANK = 4 } cr_stop;
 
 /* Square sparse matrix in CSR form (host memory): row i holds entries

@@ -21,7 +21,7 @@ _lib = None
 
 CR_OK, CR_EINVAL, CR_ENOMEM, CR_ECUDA, CR_ENOTCONV, CR_ETIMEOUT, CR_ERANK, CR_ESTATE = range(8)
 CR_FP64, CR_MIXED = 0, 1
-CR_PRECOND_JACOBI, CR_PRECOND_LEARNED, CR_PRECOND_MULTIGRID = 0, 1, 2
+CR_PRECOND_JACOBI, CR_PRECOND_LEARNED, CR_PRECOND_MULTIGRID, CR_PRECOND_AUTO = 0, 1, 2, 3
 STOP_NAMES = {0: "none", 1: "r_max", 2: "dW", 3: "relres", 4: "rank"}
 
 _dp = C.POINTER(C.c_double)

@@ -166,3 +166,21 @@ def test_too_small_for_a_hierarchy_falls_back_to_jacobi(cr):
         uh, _ = g.cr_solve_u(v, rhs)
         assert g.cr_get_stats()["pcg_multigrid"] == [0, 0]
     assert rel(uh, o.solve_u(v, rhs)) < 1e-9
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_auto_choice_per_side(cr, prec):
+    """CR_PRECOND_AUTO: multigrid on the v side; on the u side multigrid in the
+    float64 form (or above 20,000 rows), Jacobi in float32 at this size.  Either
+    way the solves meet the oracle's."""
+    p = synth.visual_cortex()
+    o = Oracle.from_problem(p)
+    v = synth.smooth_unit(p.grid_x, 101)
+    u = synth.smooth_unit(p.grid_y, 102)
+    rng = np.random.default_rng(103)
+    rhs_u = rng.standard_normal(p.ny)
+    rhs_v = rng.standard_normal(p.nx)
+    uh, vh, _, _, st = solves(cr, p, v, u, rhs_u, rhs_v, prec, cr.CR_PRECOND_AUTO)
+    assert st["pcg_multigrid"] == ([3, 3] if prec == "fp64" else [0, 3]), st["pcg_multigrid"]
+    assert rel(uh, o.solve_u(v, rhs_u)) < 1e-9
+    assert rel(vh, o.solve_v(u, rhs_v)) < 1e-9
