@@ -66,6 +66,20 @@ typedef enum {
   CR_PRECOND_MULTIGRID = 2,
   CR_PRECOND_AUTO = 3
 } cr_precond;
+/* Form of the Galerkin CG (cr_options.galerkin_form).  The projection (Eq. Proj_Sylv)
+ * it solves is the same in every form; the forms differ in the basis the CG runs
+ * in and its preconditioner.  CR_GALERKIN_EIGEN runs the CG on Qa^T Z Qb, where
+ * A1 = U^T L_y U = Qa diag(la) Qa^T and B1 = V^T L_x V = Qb diag(lb) Qb^T are
+ * diagonal (fast diagonalization): the A1 Z B1 term becomes a scaling and the
+ * preconditioner the operator's diagonal there.  Qa and Qb follow the greedy
+ * rank by one arrowhead eigen-update per new border.  The solution is checked
+ * in the original basis; if the residual is above the tolerance there, the
+ * original-basis CG finishes from it. */
+typedef enum {
+  CR_GALERKIN_AUTO = 0,   /* the eigenbasis form wherever the persistent Galerkin kernel runs */
+  CR_GALERKIN_JACOBI = 1, /* the original basis, preconditioned by diag(K) */
+  CR_GALERKIN_EIGEN = 2   /* the eigenbasis form (as AUTO) */
+} cr_galerkin_form;
 typedef enum { CR_STOP_NONE = 0, CR_STOP_RMAX = 1, CR_STOP_DW = 2, CR_STOP_RELRES = 3, CR_STOP_RANK = 4 } cr_stop;
 
 /* Square sparse matrix in CSR form (host memory): row i holds entries
@@ -151,6 +165,7 @@ typedef struct {
                               that share the GPU (cr_solve_batch) cap it so that their launches co-run. */
   int32_t learned_judge;   /* how Jacobi-PCG judges the learned preconditioner (cr_set_preconditioner):
                               0 = by time (default), 1 = by iterations */
+  int32_t galerkin_form;   /* cr_galerkin_form (default CR_GALERKIN_AUTO) */
 } cr_options;
 
 typedef struct {
@@ -205,6 +220,9 @@ typedef struct {
   int64_t pcg_cluster[2];         /* CTAs per thread-block cluster of the u-side (0) and v-side (1) PCG;
                                      0 = the grid-wide kernel */
   int64_t pcg_multigrid[2];       /* levels of the multigrid preconditioner per side (0 = not in use) */
+  int64_t galerkin_eigen[2];      /* projections solved in the eigenbasis form (0), of which the
+                                     original-basis CG had to finish (1) */
+  double galerkin_basis_ms;       /* host time spent on the eigenbasis updates (arrowhead steps) */
 } cr_stats;
 
 /* Fill *o with defaults (struct_size set).  Always succeeds for o != NULL. */

@@ -22,6 +22,7 @@ _lib = None
 CR_OK, CR_EINVAL, CR_ENOMEM, CR_ECUDA, CR_ENOTCONV, CR_ETIMEOUT, CR_ERANK, CR_ESTATE = range(8)
 CR_FP64, CR_MIXED = 0, 1
 CR_PRECOND_JACOBI, CR_PRECOND_LEARNED, CR_PRECOND_MULTIGRID, CR_PRECOND_AUTO = 0, 1, 2, 3
+CR_GALERKIN_AUTO, CR_GALERKIN_JACOBI, CR_GALERKIN_EIGEN = 0, 1, 2
 STOP_NAMES = {0: "none", 1: "r_max", 2: "dW", 3: "relres", 4: "rank"}
 
 _dp = C.POINTER(C.c_double)
@@ -58,7 +59,8 @@ class cr_options(C.Structure):
                 ("galerkin_maxit", C.c_int32), ("residual_every", C.c_int32), ("cluster_size", C.c_int32),
                 ("profile", C.c_int32), ("pcg_kernel", C.c_int32), ("galerkin_kernel", C.c_int32),
                 ("seed", C.c_uint64), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
-                ("alloc_ctx", C.c_void_p), ("galerkin_ctas", C.c_int32), ("learned_judge", C.c_int32)]
+                ("alloc_ctx", C.c_void_p), ("galerkin_ctas", C.c_int32), ("learned_judge", C.c_int32),
+                ("galerkin_form", C.c_int32)]
 
 
 class cr_rank1_info(C.Structure):
@@ -79,7 +81,8 @@ class cr_stats(C.Structure):
                 ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("phase_ms", C.c_double * 8), ("phase_calls", C.c_int64 * 8),
                 ("learned_solves", C.c_int64), ("learned_fallbacks", C.c_int64), ("learned_off", C.c_int64),
                 ("mixed_handovers", C.c_int64), ("pcg_cluster", C.c_int64 * 2),
-                ("pcg_multigrid", C.c_int64 * 2)]
+                ("pcg_multigrid", C.c_int64 * 2), ("galerkin_eigen", C.c_int64 * 2),
+                ("galerkin_basis_ms", C.c_double)]
 
 
 class cr_solve_info(C.Structure):
@@ -492,7 +495,9 @@ class ConReg:
                 "learned_solves": s.learned_solves, "learned_fallbacks": s.learned_fallbacks,
                 "learned_off": s.learned_off, "mixed_handovers": s.mixed_handovers,
                 "pcg_cluster": [s.pcg_cluster[0], s.pcg_cluster[1]],
-                "pcg_multigrid": [s.pcg_multigrid[0], s.pcg_multigrid[1]]}
+                "pcg_multigrid": [s.pcg_multigrid[0], s.pcg_multigrid[1]],
+                "galerkin_eigen": [s.galerkin_eigen[0], s.galerkin_eigen[1]],
+                "galerkin_basis_ms": s.galerkin_basis_ms}
 
     def cr_solve_u(self, v, rhs, allow_notconv: bool = False):
         """(solution, iterations); with ``allow_notconv`` a solve that stopped at

@@ -27,11 +27,13 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <vector>
 
 #include "conreg.h"
 #include "cr_common.cuh"
+#include "cr_host_arrow.h"
 #include "cr_host_linalg.h"
 #include "cr_mg_host.h"
 
@@ -198,6 +200,19 @@ struct cr_problem {
   unsigned* gbar = nullptr;
   int* gerr = nullptr;
   int gal_nb = 0;
+  // Galerkin CG in the eigenbasis of A1 and B1: eigenvectors Qa, Qb (each with a
+  // second buffer for the update; zero outside the leading eq x eq block),
+  // eigenvalues (host and device), transformed matrices and work.  eq = borders
+  // taken into the bases so far.
+  double *eQa = nullptr, *eQa2 = nullptr, *eQb = nullptr, *eQb2 = nullptr, *ela = nullptr, *elb = nullptr;
+  double *eA2t = nullptr, *eB2t = nullptr, *eFt = nullptr, *eZt = nullptr, *eDen = nullptr, *eTmp = nullptr;
+  double *eHt = nullptr, *eY = nullptr, *eGt = nullptr, *eg = nullptr, *eW = nullptr, *ebord = nullptr;
+  double* eh = nullptr;  // pinned staging: borders, W_a, W_b, la, lb
+  float *fQa = nullptr, *fla = nullptr, *flb = nullptr, *fY = nullptr, *fGt = nullptr;
+  std::vector<double> hla, hlb;
+  int eq = 0;
+  int64_t gal_eig_proj = 0, gal_eig_finish = 0;
+  double gal_basis_ms = 0.0;
   // float32 copies for the mixed form's inner Galerkin CG
   // learned preconditioner: box index of each row per side, the network, its buffers
   int* box[2] = {nullptr, nullptr};
@@ -1211,6 +1226,105 @@ cr_status mixed_G(cr_problem* p, bool tensor_cores = false) {
   return CR_OK;
 }
 
+// Eigenbases of A1 = U^T L_y U and B1 = V^T L_x V, brought up to the current
+// rank one border at a time.  With A1 = Qa diag(la) Qa^T, the bordered matrix
+// [A1 a; a^T alpha] equals blockdiag(Qa, 1) M blockdiag(Qa, 1)^T for the
+// arrowhead M of (la, Qa^T a, alpha); with M = W diag(mu) W^T the new basis is
+// blockdiag(Qa, 1) W and the new eigenvalues mu.  The arrowhead step runs on the
+// host (cr_host::arrow_eig, O(q^2)); the product with W on the device.
+cr_status eig_sync(cr_problem* p) {
+  cudaStream_t st = p->st;
+  const int64_t ld = p->rcap;
+  const int j = p->j;
+  if (p->eq >= j) return CR_OK;
+  const auto t0 = std::chrono::steady_clock::now();
+  double* hb = p->eh;                         // borders: a side at [0, ld + 1), b side after
+  double* hW = hb + 2 * (ld + 1);             // W_a, then W_b (each (q+1)^2, column-major)
+  double* hl = hW + 2 * ld * ld;              // la, lb
+  std::vector<double> mua, mub, Wa, Wb;
+  while (p->eq < j) {
+    const int q = p->eq, n1 = q + 1;
+    fill(1, 1.0, p->eQa + q + q * ld, st);   // blockdiag(Qa, 1): the rest of row and column q is zero
+    fill(1, 1.0, p->eQb + q + q * ld, st);
+    if (q > 0) {
+      gemv_t(q, q, p->eQa, ld, p->A1 + q * ld, p->ebord, 1, 1.0, 0.0, st);
+      gemv_t(q, q, p->eQb, ld, p->B1 + q * ld, p->ebord + ld + 1, 1, 1.0, 0.0, st);
+    }
+    copy(1, p->A1 + q + q * ld, p->ebord + q, st);
+    copy(1, p->B1 + q + q * ld, p->ebord + ld + 1 + q, st);
+    CUCHK(p, cudaMemcpyAsync(hb, p->ebord, sizeof(double) * 2 * (ld + 1), cudaMemcpyDeviceToHost, st));
+    p->d2h_bytes += (int64_t)sizeof(double) * 2 * (ld + 1);
+    TRY(sync(p));
+    const std::vector<double> za(hb, hb + q), zb(hb + ld + 1, hb + ld + 1 + q);
+    std::thread tb([&]() { cr_host::arrow_eig(q, p->hlb, zb, hb[ld + 1 + q], mub, Wb); });
+    cr_host::arrow_eig(q, p->hla, za, hb[q], mua, Wa);
+    tb.join();
+    std::copy(Wa.begin(), Wa.end(), hW);
+    std::copy(Wb.begin(), Wb.end(), hW + (size_t)n1 * n1);
+    CUCHK(p, cudaMemcpyAsync(p->eW, hW, sizeof(double) * 2 * n1 * n1, cudaMemcpyHostToDevice, st));
+    p->h2d_bytes += (int64_t)sizeof(double) * 2 * n1 * n1;
+    gemm(n1, n1, n1, 1.0, MatView{p->eQa, 1, ld}, MatView{p->eW, 1, n1}, 0.0, p->eQa2, 1, ld, p->ws, p->ws_elems,
+         st);
+    gemm(n1, n1, n1, 1.0, MatView{p->eQb, 1, ld}, MatView{p->eW + (size_t)n1 * n1, 1, n1}, 0.0, p->eQb2, 1, ld,
+         p->ws, p->ws_elems, st);
+    std::swap(p->eQa, p->eQa2);
+    std::swap(p->eQb, p->eQb2);
+    p->hla = mua;
+    p->hlb = mub;
+    ++p->eq;
+  }
+  std::copy(p->hla.begin(), p->hla.end(), hl);
+  std::copy(p->hlb.begin(), p->hlb.end(), hl + ld);
+  CUCHK(p, cudaMemcpyAsync(p->ela, hl, sizeof(double) * j, cudaMemcpyHostToDevice, st));
+  CUCHK(p, cudaMemcpyAsync(p->elb, hl + ld, sizeof(double) * j, cudaMemcpyHostToDevice, st));
+  p->h2d_bytes += (int64_t)sizeof(double) * 2 * j;
+  TRY(sync(p));  // the staging buffer is reused by the next call
+  p->gal_basis_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return CR_OK;
+}
+
+// Forget the eigenbases (the factors were replaced); the next projection
+// rebuilds them border by border.
+void eig_reset(cr_problem* p) {
+  if (!p->eQa) return;
+  const int64_t ld = p->rcap;
+  for (double* b : {p->eQa, p->eQa2, p->eQb, p->eQb2}) fill(ld * ld, 0.0, b, p->st);
+  p->hla.clear();
+  p->hlb.clear();
+  p->eq = 0;
+}
+
+bool gal_eigen(const cr_problem* p) {
+  return p->eQa && p->j > 0 && (p->opt.precision == CR_MIXED || p->opt.galerkin_kernel == 0);
+}
+
+// C = Qa^T S Qb (to_eig) or C = Qa S Qb^T (from_eig), through eTmp.
+void eig_transform(cr_problem* p, const double* S, double* C, bool to_eig, double beta = 0.0) {
+  const int j = p->j;
+  const int64_t ld = p->rcap;
+  if (to_eig) {
+    gemm(j, j, j, 1.0, MatView{p->eQa, ld, 1}, MatView{S, 1, ld}, 0.0, p->eTmp, 1, ld, p->ws, p->ws_elems, p->st);
+    gemm(j, j, j, 1.0, MatView{p->eTmp, 1, ld}, MatView{p->eQb, 1, ld}, beta, C, 1, ld, p->ws, p->ws_elems, p->st);
+  } else {
+    gemm(j, j, j, 1.0, MatView{p->eQa, 1, ld}, MatView{S, 1, ld}, 0.0, p->eTmp, 1, ld, p->ws, p->ws_elems, p->st);
+    gemm(j, j, j, 1.0, MatView{p->eTmp, 1, ld}, MatView{p->eQb, ld, 1}, beta, C, 1, ld, p->ws, p->ws_elems, p->st);
+  }
+}
+
+// The eigenbasis operator's matrices: A2t = Qa^T A2 Qa, B2t = Qb^T B2 Qb,
+// Ht = Qb^T H, and the preconditioner's diagonal.
+void eig_operator(cr_problem* p) {
+  cudaStream_t st = p->st;
+  const int j = p->j, m = p->m;
+  const int64_t ld = p->rcap;
+  gemm(j, j, j, 1.0, MatView{p->eQa, ld, 1}, MatView{p->A2, 1, ld}, 0.0, p->eTmp, 1, ld, p->ws, p->ws_elems, st);
+  gemm(j, j, j, 1.0, MatView{p->eTmp, 1, ld}, MatView{p->eQa, 1, ld}, 0.0, p->eA2t, 1, ld, p->ws, p->ws_elems, st);
+  gemm(j, j, j, 1.0, MatView{p->eQb, ld, 1}, MatView{p->B2, 1, ld}, 0.0, p->eTmp, 1, ld, p->ws, p->ws_elems, st);
+  gemm(j, j, j, 1.0, MatView{p->eTmp, 1, ld}, MatView{p->eQb, 1, ld}, 0.0, p->eB2t, 1, ld, p->ws, p->ws_elems, st);
+  gemm(j, m, j, 1.0, MatView{p->eQb, ld, 1}, MatView{p->H, 1, ld}, 0.0, p->eHt, 1, ld, p->ws, p->ws_elems, st);
+  galerkin_eig_diag(j, m, ld, p->lam, p->eA2t, p->eB2t, p->ela, p->elb, p->G, p->eHt, p->eg, p->eDen, st);
+}
+
 cr_status do_project(cr_problem* p, double tol, cr_proj_info* info) {
   cudaStream_t st = p->st;
   const int j = p->j;
@@ -1226,6 +1340,11 @@ cr_status do_project(cr_problem* p, double tol, cr_proj_info* info) {
   int k = 0;
   double fn2 = 0.0, rr = 0.0;
   cr_status rc = CR_OK;
+  const bool eig = gal_eigen(p);
+  if (eig) {
+    TRY(eig_sync(p));
+    eig_operator(p);
+  }
   if (p->opt.precision == CR_MIXED && p->gal_nb > 0) {
     // Mixed form: float64 iterative refinement.  Each outer step forms the
     // float64 residual R = F - K(Z) and solves K dZ = R to about 3e-4 relative
@@ -1237,13 +1356,31 @@ cr_status do_project(cr_problem* p, double tol, cr_proj_info* info) {
     TRY(readback(p, DS_GS + 3, 1, false));
     fn2 = p->hs->ds[DS_GS + 3];
     const int64_t r2 = ld * ld;
-    to_f32(r2, p->A1, p->fA1, st);
-    to_f32(r2, p->A2, p->fA2, st);
-    to_f32(r2, p->B1, p->fB1, st);
-    to_f32(r2, p->B2, p->fB2, st);
-    to_f32(r2, p->gDg, p->fDg, st);
-    to_f32(ld * p->m, p->H, p->fH, st);
+    if (eig) {
+      // the inner float32 CG runs in the eigenbasis; the float64 residual stays in the original one
+      to_f32(r2, p->eA2t, p->fA2, st);
+      to_f32(r2, p->eB2t, p->fB2, st);
+      to_f32(r2, p->eDen, p->fDg, st);
+      to_f32(ld * p->m, p->eHt, p->fH, st);
+      to_f32(r2, p->eQa, p->fQa, st);
+      to_f32(ld, p->ela, p->fla, st);
+      to_f32(ld, p->elb, p->flb, st);
+      ++p->gal_eig_proj;
+    } else {
+      to_f32(r2, p->A1, p->fA1, st);
+      to_f32(r2, p->A2, p->fA2, st);
+      to_f32(r2, p->B1, p->fB1, st);
+      to_f32(r2, p->B2, p->fB2, st);
+      to_f32(r2, p->gDg, p->fDg, st);
+      to_f32(ld * p->m, p->H, p->fH, st);
+    }
     TRY(mixed_G(p));
+    GalEig<float> fe;
+    fe.Qa = p->fQa;
+    fe.la = p->fla;
+    fe.lb = p->flb;
+    fe.Y = p->fY;
+    fe.Gt = p->fGt;
     for (int outer = 0; outer < 40 && fn2 > 0.0; ++outer) {
       galerkin_apply(p, p->Z, p->gQ);
       mat_axpby(j, j, 1.0, p->F, ld, -1.0, p->gQ, ld, p->gR, ld, st);
@@ -1255,17 +1392,25 @@ cr_status do_project(cr_problem* p, double tol, cr_proj_info* info) {
         rc = fail(p, CR_ENOTCONV, "mixed Galerkin refinement produced a non-finite residual");
         break;
       }
-      to_f32(r2, p->gR, p->fF, st);
+      if (eig) {
+        eig_transform(p, p->gR, p->eFt, true);
+        to_f32(r2, p->eFt, p->fF, st);
+      } else {
+        to_f32(r2, p->gR, p->fF, st);
+      }
       CUCHK(p, cudaMemsetAsync(p->fZ, 0, sizeof(float) * r2, st));
       CUCHK(p, cudaMemsetAsync(p->gbar, 0, 2 * sizeof(unsigned), st));
       CUCHK(p, cudaMemsetAsync(p->gerr, 0, sizeof(int), st));
-      cudaError_t ce = galerkin_cluster_f32_launch(j, p->m, ld, p->lam, p->fA1, p->fA2, p->fB1, p->fB2, p->fG,
-                                                   p->fH, p->fF, p->fDg, p->fZ, 1e-7 * rr, maxit, p->gout, st);
+      cudaError_t ce = cudaErrorNotSupported;
+      if (!eig)
+        ce = galerkin_cluster_f32_launch(j, p->m, ld, p->lam, p->fA1, p->fA2, p->fB1, p->fB2, p->fG, p->fH, p->fF,
+                                         p->fDg, p->fZ, 1e-7 * rr, maxit, p->gout, st);
       if (ce == cudaErrorNotSupported) {
         cudaGetLastError();
         ce = galerkin_cg_launch<float>(p->gal_nb, j, p->m, ld, p->lam, p->fA1, p->fA2, p->fB1, p->fB2, p->fG, p->fH,
                                        p->fF, p->fDg, p->fZ, p->fR, p->fPa, p->fPb, p->fQ, p->fT2, p->fT1, p->fTH,
-                                       p->fGw, p->fzb, p->gpart, p->gbar, p->gerr, 1e-7 * rr, maxit, p->gout, st);
+                                       p->fGw, p->fzb, p->gpart, p->gbar, p->gerr, 1e-7 * rr, maxit, p->gout, st,
+                                       eig ? &fe : nullptr);
       }
       CUCHK(p, ce);
       double out[3] = {0, 0, 0};
@@ -1274,7 +1419,13 @@ cr_status do_project(cr_problem* p, double tol, cr_proj_info* info) {
       TRY(sync(p));
       k += (int)out[0];
       if (out[2] == 3.0) return fail(p, CR_ETIMEOUT, "Galerkin CG grid barrier timed out");
-      add_f32(j, j, p->fZ, ld, p->Z, ld, st);
+      if (eig) {  // Z += Qa dZt Qb^T
+        fill(r2, 0.0, p->eZt, st);
+        add_f32(j, j, p->fZ, ld, p->eZt, ld, st);
+        eig_transform(p, p->eZt, p->Z, false, 1.0);
+      } else {
+        add_f32(j, j, p->fZ, ld, p->Z, ld, st);
+      }
       if (outer == 39) rc = fail(p, CR_ENOTCONV, "mixed Galerkin refinement did not converge");
     }
   } else if (p->opt.galerkin_kernel == 0 && p->gal_nb > 0) {
@@ -1282,7 +1433,41 @@ cr_status do_project(cr_problem* p, double tol, cr_proj_info* info) {
     mat_dot(j, j, p->F, ld, p->F, ld, gs + 3, st);
     TRY(readback(p, DS_GS + 3, 1, false));
     fn2 = p->hs->ds[DS_GS + 3];
-    if (fn2 > 0.0) {
+    bool done = false;
+    if (eig && fn2 > 0.0) {
+      // CG on Zt = Qa^T Z Qb from the transformed warm start, then Z = Qa Zt Qb^T
+      // and its residual in the original basis
+      eig_transform(p, p->F, p->eFt, true);
+      eig_transform(p, p->Z, p->eZt, true);
+      GalEig<double> ge;
+      ge.Qa = p->eQa;
+      ge.la = p->ela;
+      ge.lb = p->elb;
+      ge.Y = p->eY;
+      ge.Gt = p->eGt;
+      CUCHK(p, cudaMemsetAsync(p->gbar, 0, 2 * sizeof(unsigned), st));
+      CUCHK(p, cudaMemsetAsync(p->gerr, 0, sizeof(int), st));
+      CUCHK(p, galerkin_cg_launch(p->gal_nb, j, p->m, ld, p->lam, p->A1, p->eA2t, p->B1, p->eB2t, p->G, p->eHt,
+                                  p->eFt, p->eDen, p->eZt, p->gR, p->gP, p->gT, p->gQ, p->gZB2, p->gZB1, p->gZH,
+                                  p->gGw, p->gzb, p->gpart, p->gbar, p->gerr, tol * tol * fn2, maxit, p->gout, st,
+                                  &ge));
+      double out[3] = {0, 0, 0};
+      CUCHK(p, cudaMemcpyAsync(out, p->gout, sizeof(out), cudaMemcpyDeviceToHost, st));
+      p->d2h_bytes += (int64_t)sizeof(out);
+      TRY(sync(p));
+      k = (int)out[0];
+      if (out[2] == 3.0) return fail(p, CR_ETIMEOUT, "Galerkin CG grid barrier timed out");
+      eig_transform(p, p->eZt, p->Z, false);
+      galerkin_apply(p, p->Z, p->gQ);
+      mat_axpby(j, j, 1.0, p->F, ld, -1.0, p->gQ, ld, p->gR, ld, st);
+      mat_dot(j, j, p->gR, ld, p->gR, ld, gs + 4, st);
+      TRY(readback(p, DS_GS + 4, 1, false));
+      rr = p->hs->ds[DS_GS + 4];
+      ++p->gal_eig_proj;
+      done = rr <= tol * tol * fn2;
+      if (!done) ++p->gal_eig_finish;
+    }
+    if (fn2 > 0.0 && !done) {
       CUCHK(p, cudaMemsetAsync(p->gbar, 0, 2 * sizeof(unsigned), st));
       CUCHK(p, cudaMemsetAsync(p->gerr, 0, sizeof(int), st));
       CUCHK(p, galerkin_cg_launch(p->gal_nb, j, p->m, ld, p->lam, p->A1, p->A2, p->B1, p->B2, p->G, p->H, p->F,
@@ -1292,7 +1477,7 @@ cr_status do_project(cr_problem* p, double tol, cr_proj_info* info) {
       CUCHK(p, cudaMemcpyAsync(out, p->gout, sizeof(out), cudaMemcpyDeviceToHost, st));
       p->d2h_bytes += (int64_t)sizeof(out);
       TRY(sync(p));
-      k = (int)out[0];
+      k += (int)out[0];
       rr = out[1];
       if (out[2] == 1.0) rc = fail(p, CR_ENOTCONV, "Galerkin CG reached its iteration cap");
       if (out[2] == 2.0) rc = fail(p, CR_ENOTCONV, "Galerkin CG broke down (non-positive curvature)");
@@ -1618,6 +1803,7 @@ void cr_destroy(cr_problem* p) {
       cudaFree(a.first);
   }
   if (p->hs) cudaFreeHost(p->hs);
+  if (p->eh) cudaFreeHost(p->eh);
   prof_resolve(p);
   for (auto e : p->ev_pool) cudaEventDestroy(e);
   for (auto e : p->open_ev)
@@ -1659,6 +1845,8 @@ cr_status cr_create(const cr_problem_desc* d_in, const cr_options* o, cr_problem
   if (opt.r_cap < 1 || opt.r_cap > std::min(nx, ny)) return bad("r_cap must be in [1, min(nx, ny)]");
   if (!(opt.pcg_tol > 0.0) || opt.pcg_maxit < 1 || opt.als_max_iter < 1 || !(opt.als_delta >= 0.0))
     return bad("bad solver options");
+  if (opt.galerkin_form < CR_GALERKIN_AUTO || opt.galerkin_form > CR_GALERKIN_EIGEN)
+    return bad("galerkin_form must be a cr_galerkin_form");
   if (opt.alloc && !opt.free) return bad("alloc given without free");
   std::string err;
   if (check_csr(d->Lx, nx, "Lx", err) != CR_OK || check_csr(d->Ly, ny, "Ly", err) != CR_OK) return bad(err);
@@ -1828,6 +2016,27 @@ cr_status cr_create(const cr_problem_desc* d_in, const cr_options* o, cr_problem
   CK(dalloc(p, &p->gout, 4));
   CK(dalloc(p, &p->gbar, 2));
   CK(dalloc(p, &p->gerr, 1));
+  if (p->gal_nb > 0 && opt.galerkin_form != CR_GALERKIN_JACOBI) {
+    for (double** b : {&p->eQa, &p->eQa2, &p->eQb, &p->eQb2, &p->eA2t, &p->eB2t, &p->eFt, &p->eZt, &p->eDen,
+                       &p->eTmp})
+      CK(dalloc(p, b, r2));
+    for (double** b : {&p->eHt, &p->eY, &p->eGt}) CK(dalloc(p, b, (size_t)rc * m));
+    for (double** b : {&p->ela, &p->elb}) CK(dalloc(p, b, rc));
+    CK(dalloc(p, &p->eg, m));
+    CK(dalloc(p, &p->eW, 2 * r2));
+    CK(dalloc(p, &p->ebord, 2 * ((size_t)rc + 1)));
+    if (cudaMallocHost(&p->eh, sizeof(double) * (2 * ((size_t)rc + 1) + 2 * r2 + 2 * (size_t)rc)) != cudaSuccess) {
+      cudaGetLastError();
+      p->eh = nullptr;
+      p->err = "cudaMallocHost failed";
+      return abort_create(CR_ENOMEM);
+    }
+    if (opt.precision == CR_MIXED) {
+      CK(dalloc(p, &p->fQa, r2));
+      for (float** b : {&p->fla, &p->flb}) CK(dalloc(p, b, rc));
+      for (float** b : {&p->fY, &p->fGt}) CK(dalloc(p, b, (size_t)rc * m));
+    }
+  }
   if (opt.precision == CR_MIXED) {
     for (float** b : {&p->fA1, &p->fA2, &p->fB1, &p->fB2, &p->fDg, &p->fF, &p->fZ, &p->fR, &p->fPa, &p->fPb, &p->fQ,
                       &p->fT2, &p->fT1, &p->fzb})
@@ -2039,6 +2248,9 @@ cr_status cr_get_stats(cr_problem* p, cr_stats* s, int32_t reset) {
     s->pcg_cluster[side] = (use_mg(p, side, f32) || !use_grid_pcg(p, side, f32)) ? L.csize : 0;
     s->pcg_multigrid[side] = use_mg(p, side, f32) ? p->mg[side].nlev : 0;
   }
+  s->galerkin_eigen[0] = p->gal_eig_proj;
+  s->galerkin_eigen[1] = p->gal_eig_finish;
+  s->galerkin_basis_ms = p->gal_basis_ms;
   for (int i = 0; i < CR_NPHASE; ++i) {
     s->phase_ms[i] = p->phase_ms[i];
     s->phase_calls[i] = p->phase_calls[i];
@@ -2048,6 +2260,8 @@ cr_status cr_get_stats(cr_problem* p, cr_stats* s, int32_t reset) {
     p->pcg_solves = p->pcg_iters = 0;
     p->h2d_bytes = p->d2h_bytes = 0;
     p->learned_solves = p->fcg_fallbacks = p->mixed_handovers = 0;
+    p->gal_eig_proj = p->gal_eig_finish = 0;
+    p->gal_basis_ms = 0.0;
     for (int i = 0; i < CR_NPHASE; ++i) {
       p->phase_ms[i] = 0.0;
       p->phase_calls[i] = 0;
@@ -2240,6 +2454,7 @@ cr_status cr_set_factors(cr_problem* p, int32_t j, const double* U, int64_t ldu,
   p->nQL = 0;
   p->nQR = p->nQX;  // the X part of the right basis does not depend on the factors
   p->j = 0;
+  eig_reset(p);
   if (j > 0) {
     CUCHK(p, cudaMemcpy2DAsync(p->UU, 3 * (size_t)p->ny * sizeof(double), U, ldu * sizeof(double),
                                p->ny * sizeof(double), j, cudaMemcpyHostToDevice, st));

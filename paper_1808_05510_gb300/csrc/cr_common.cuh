@@ -265,12 +265,27 @@ void batched_gemv(int j, int m, const double* G, int64_t ldg, int64_t gstride, c
 // ---------------------------------------------------------------- cr_galerkin.cu
 // CTAs of the persistent Galerkin CG (one per SM), 0 if the kernel cannot run.
 int galerkin_grid_size();
-// T = double (float64 form) or float (inner solve of the mixed form)
+// Eigenbasis form of the Galerkin CG: Qa (j x j, ld) the eigenvectors of A1,
+// la, lb the eigenvalues of A1 and B1; Y, Gt ld x m work.  The launch's A2, B2,
+// H, F, Z and Dg are then the transformed A2t, B2t, Ht, Ft, Zt and diagonal.
+template <class T>
+struct GalEig {
+  const T *Qa = nullptr, *la = nullptr, *lb = nullptr;
+  T *Y = nullptr, *Gt = nullptr;
+};
+// Diagonal of the eigenbasis Galerkin operator with each G_a replaced by its mean
+// diagonal g_a = tr(G_a) / j (g: m doubles, written):
+//   Den(i, k) = lam (A2t_ii + 2 la_i lb_k + B2t_kk) + sum_a g_a Ht(k, a)^2
+void galerkin_eig_diag(int j, int m, int64_t ld, double lam, const double* A2t, const double* B2t, const double* la,
+                       const double* lb, const double* G, const double* Ht, double* g, double* Den,
+                       cudaStream_t st);
+// T = double (float64 form) or float (inner solve of the mixed form); eig = nullptr: original basis
 template <class T>
 cudaError_t galerkin_cg_launch(int nb, int j, int m, int64_t ld, double lam, const T* A1, const T* A2, const T* B1,
                                const T* B2, const T* G, const T* H, const T* F, const T* Dg, T* Z, T* R, T* Pa,
                                T* Pb, T* Q, T* T2, T* T1, T* TH, T* Gw, T* zb, double* part, unsigned* bar,
-                               int* err, double tol2, int maxit, double* out, cudaStream_t st);
+                               int* err, double tol2, int maxit, double* out, cudaStream_t st,
+                               const GalEig<T>* eig = nullptr);
 
 // Single-cluster float32 Galerkin CG (inner solves of the mixed form, j <= 128,
 // m <= 128); cudaErrorNotSupported when the sizes do not fit.  Solves

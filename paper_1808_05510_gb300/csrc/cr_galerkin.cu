@@ -11,6 +11,20 @@
 //   C  Q = lam T2 + 2 lam A1 T1 + lam A2 X + Gw H^T  (8x8 tiles) and <X, Q>
 //   D  alpha; Z += alpha X; R -= alpha Q; z = R ./ diag(K); <R, z>, <R, R>
 //   E  beta; X_next = z + beta X
+// Eigenbasis form (fast diagonalization).  With A1 = Qa diag(la) Qa^T and
+// B1 = Qb diag(lb) Qb^T (A1 = U^T L_y U, B1 = V^T L_x V), the CG runs on
+// Zt = Qa^T Z Qb, where the operator is
+//   Kt(X) = lam (X B2t + 2 diag(la) X diag(lb) + A2t X) + Qa^T [G_a Qa X ht_a] ht_a^T
+// with A2t = Qa^T A2 Qa, B2t = Qb^T B2 Qb, ht_a = Qb^T h_a: the A1 X B1 product
+// becomes a scaling, two of the four j^3 products per iteration go, and the data
+// term needs two thin (j x m) products more:
+//   A  T2 = X B2t, TH = X Ht
+//   A' Y = Qa TH
+//   B  Gw(:, a) = G_a Y(:, a)
+//   B' Gt = Qa^T Gw
+//   C  Q = lam T2 + 2 lam la_i lb_l X + lam A2t X + Gt Ht^T
+// Dg then holds the diagonal of Kt with the data term's G_a replaced by its mean
+// diagonal (an SPD preconditioner; the iterate it converges to is the same).
 // Tiles use all CTAs; each output is summed in a fixed order (k split in four
 // fixed ranges added in order), and every CTA adds the per-CTA partial sums of
 // the inner products in block order, so all CTAs take the same decisions and
@@ -42,6 +56,9 @@ struct GalArgs {
   double tol2;         // stop when |R|^2 <= tol2
   int maxit;
   double* out;         // [0] iterations, [1] |R|^2, [2] status (0 ok, 1 cap, 2 breakdown, 3 barrier timeout)
+  // eigenbasis form (Qa == nullptr: the original basis); A1, B1 unused there
+  const T *Qa, *la, *lb;
+  T *Yb, *Gt;  // ld x m work
 };
 
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
@@ -174,22 +191,25 @@ __device__ __forceinline__ T tile_reduce(T acc, bool& valid) {
   return v;
 }
 
-// K(X) -> Q for X = Xin (phases A, B, C); returns <X, Q> partial of this CTA in pq.
+// K(X) -> Q for X = Xin (phases A, B, C; A' and B' in the eigenbasis form);
+// returns <X, Q> partial of this CTA in pq.
 template <class T>
 __device__ bool apply_K(const GalArgs<T>& a, const T* X, double& pq) {
   const int j = a.j, m = a.m;
   const int64_t ld = a.ld;
   const int nt = (j + TS - 1) / TS, ntm = (m + TS - 1) / TS;
+  const bool eig = a.Qa != nullptr;
   // A
-  const int itemsA = 2 * nt * nt + nt * ntm;
+  const int nA = eig ? 1 : 2;
+  const int itemsA = nA * nt * nt + nt * ntm;
   for (int it = blockIdx.x; it < itemsA; it += a.nb) {
     int which, ti, tl;
     if (it < nt * nt) {
       which = 0; ti = it % nt; tl = it / nt;
-    } else if (it < 2 * nt * nt) {
+    } else if (it < nA * nt * nt) {
       which = 1; ti = (it - nt * nt) % nt; tl = (it - nt * nt) / nt;
     } else {
-      which = 2; ti = (it - 2 * nt * nt) % nt; tl = (it - 2 * nt * nt) / nt;
+      which = 2; ti = (it - nA * nt * nt) % nt; tl = (it - nA * nt * nt) / nt;
     }
     const int N = which == 2 ? m : j;
     const T* Bm = which == 0 ? a.B2 : which == 1 ? a.B1 : a.H;
@@ -204,7 +224,23 @@ __device__ bool apply_K(const GalArgs<T>& a, const T* X, double& pq) {
     }
   }
   if (!grid_barrier(a)) return false;
+  // A' (eigenbasis): Y = Qa TH
+  if (eig) {
+    for (int it = blockIdx.x; it < nt * ntm; it += a.nb) {
+      const int ti = it % nt, tl = it / nt;
+      T acc = tile_term<T>(ti * TS, tl * TS, j, m, j, [&](int i, int k) { return a.Qa[i + k * ld]; },
+                           [&](int k, int l) { return ldcg(a.TH + k + l * ld); }, (T)0);
+      bool v;
+      const T r = tile_reduce<T>(acc, v);
+      if (v) {
+        const int i = ti * TS + (threadIdx.x & 7), l = tl * TS + (threadIdx.x >> 3);
+        if (i < j && l < m) a.Yb[i + l * ld] = r;
+      }
+    }
+    if (!grid_barrier(a)) return false;
+  }
   // B
+  const T* src = eig ? a.Yb : a.TH;
   const int nr = (j + 63) / 64;
   for (int it = blockIdx.x; it < m * nr; it += a.nb) {
     const int al = it / nr, rt = it % nr;
@@ -213,7 +249,7 @@ __device__ bool apply_K(const GalArgs<T>& a, const T* X, double& pq) {
     T acc = (T)0;
     if (i < j) {
       const int q0 = g * ((j + 3) / 4), q1 = min(j, q0 + (j + 3) / 4);
-      for (int q = q0; q < q1; ++q) acc = fma(Ga[i + q * ld], ldcg(a.TH + q + al * ld), acc);
+      for (int q = q0; q < q1; ++q) acc = fma(Ga[i + q * ld], ldcg(src + q + al * ld), acc);
     }
     __shared__ T rb[4][64];
     rb[g][threadIdx.x & 63] = acc;
@@ -223,7 +259,23 @@ __device__ bool apply_K(const GalArgs<T>& a, const T* X, double& pq) {
     __syncthreads();
   }
   if (!grid_barrier(a)) return false;
+  // B' (eigenbasis): Gt = Qa^T Gw
+  if (eig) {
+    for (int it = blockIdx.x; it < nt * ntm; it += a.nb) {
+      const int ti = it % nt, tl = it / nt;
+      T acc = tile_term<T>(ti * TS, tl * TS, j, m, j, [&](int i, int k) { return a.Qa[k + i * ld]; },
+                           [&](int k, int l) { return ldcg(a.Gw + k + l * ld); }, (T)0);
+      bool v;
+      const T r = tile_reduce<T>(acc, v);
+      if (v) {
+        const int i = ti * TS + (threadIdx.x & 7), l = tl * TS + (threadIdx.x >> 3);
+        if (i < j && l < m) a.Gt[i + l * ld] = r;
+      }
+    }
+    if (!grid_barrier(a)) return false;
+  }
   // C
+  const T* gdat = eig ? a.Gt : a.Gw;
   double dotpq = 0.0;
   const T lam = (T)a.lam;
   const T lam2 = (T)(2.0 * a.lam);
@@ -231,11 +283,12 @@ __device__ bool apply_K(const GalArgs<T>& a, const T* X, double& pq) {
     const int ti = it % nt, tl = it / nt;
     const int i0 = ti * TS, l0 = tl * TS;
     T acc = (T)0;
-    acc = tile_term<T>(i0, l0, j, j, j, [&](int i, int k) { return lam2 * a.A1[i + k * ld]; },
-                       [&](int k, int l) { return ldcg(a.T1 + k + l * ld); }, acc);
+    if (!eig)
+      acc = tile_term<T>(i0, l0, j, j, j, [&](int i, int k) { return lam2 * a.A1[i + k * ld]; },
+                         [&](int k, int l) { return ldcg(a.T1 + k + l * ld); }, acc);
     acc = tile_term<T>(i0, l0, j, j, j, [&](int i, int k) { return lam * a.A2[i + k * ld]; },
                        [&](int k, int l) { return ldcg(X + k + l * ld); }, acc);
-    acc = tile_term<T>(i0, l0, j, j, m, [&](int i, int k) { return ldcg(a.Gw + i + k * ld); },
+    acc = tile_term<T>(i0, l0, j, j, m, [&](int i, int k) { return ldcg(gdat + i + k * ld); },
                        [&](int k, int l) { return a.H[l + k * ld]; }, acc);
     bool v;
     const T r = tile_reduce<T>(acc, v);
@@ -243,9 +296,11 @@ __device__ bool apply_K(const GalArgs<T>& a, const T* X, double& pq) {
       const int i = i0 + (threadIdx.x & 7), l = l0 + (threadIdx.x >> 3);
       if (i < j && l < j) {
         const int64_t o = i + l * ld;
-        const T q = fma(lam, ldcg(a.T2 + o), r);
+        const T x = ldcg(X + o);
+        T q = fma(lam, ldcg(a.T2 + o), r);
+        if (eig) q = fma(lam2 * a.la[i] * a.lb[l], x, q);
         a.Q[o] = q;
-        dotpq += (double)ldcg(X + o) * (double)q;
+        dotpq += (double)x * (double)q;
       }
     }
   }
@@ -354,6 +409,55 @@ timeout:
 
 }  // namespace
 
+namespace {
+// g_a = tr(G_a) / j, one CTA per a
+__global__ void gal_trace_kernel(int j, int64_t ld, const double* __restrict__ G, double* __restrict__ g) {
+  const double* Ga = G + (int64_t)blockIdx.x * ld * ld;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < j; i += blockDim.x) s += Ga[i + (int64_t)i * ld];
+  __shared__ double red[32];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    g[blockIdx.x] = t / (double)j;
+  }
+}
+
+// Den(i, k) = lam (A2t_ii + 2 la_i lb_k + B2t_kk) + sum_a g_a Ht(k, a)^2
+__global__ void gal_eig_den_kernel(int j, int m, int64_t ld, double lam, const double* __restrict__ A2t,
+                                   const double* __restrict__ B2t, const double* __restrict__ la,
+                                   const double* __restrict__ lb, const double* __restrict__ g,
+                                   const double* __restrict__ Ht, double* __restrict__ Den) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)j * j) return;
+  const int i = (int)(t % j), k = (int)(t / j);
+  double h = 0.0;
+  for (int a = 0; a < m; ++a) {
+    const double x = Ht[k + (int64_t)a * ld];
+    h = fma(g[a] * x, x, h);
+  }
+  const double li = fmax(la[i], 0.0), lk = fmax(lb[k], 0.0);  // A1, B1 are positive semidefinite
+  Den[i + (int64_t)k * ld] =
+      lam * (A2t[i + (int64_t)i * ld] + 2.0 * li * lk + B2t[k + (int64_t)k * ld]) + h;
+}
+}  // namespace
+
+void galerkin_eig_diag(int j, int m, int64_t ld, double lam, const double* A2t, const double* B2t, const double* la,
+                       const double* lb, const double* G, const double* Ht, double* g, double* Den,
+                       cudaStream_t st) {
+  if (j <= 0) return;
+  if (m > 0) {
+    count_launch();
+    gal_trace_kernel<<<m, 256, 0, st>>>(j, ld, G, g);
+  }
+  const int64_t tot = (int64_t)j * j;
+  count_launch();
+  gal_eig_den_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(j, m, ld, lam, A2t, B2t, la, lb, g, Ht, Den);
+}
+
 int galerkin_grid_size() {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
@@ -370,8 +474,15 @@ template <class T>
 cudaError_t galerkin_cg_launch(int nb, int j, int m, int64_t ld, double lam, const T* A1, const T* A2, const T* B1,
                                const T* B2, const T* G, const T* H, const T* F, const T* Dg, T* Z, T* R, T* Pa,
                                T* Pb, T* Q, T* T2, T* T1, T* TH, T* Gw, T* zb, double* part, unsigned* bar,
-                               int* err, double tol2, int maxit, double* out, cudaStream_t st) {
+                               int* err, double tol2, int maxit, double* out, cudaStream_t st, const GalEig<T>* eig) {
   GalArgs<T> a{};
+  if (eig) {
+    a.Qa = eig->Qa;
+    a.la = eig->la;
+    a.lb = eig->lb;
+    a.Yb = eig->Y;
+    a.Gt = eig->Gt;
+  }
   a.j = j;
   a.m = m;
   a.nb = nb;
@@ -410,12 +521,13 @@ template cudaError_t galerkin_cg_launch<double>(int, int, int, int64_t, double, 
                                                 const double*, const double*, const double*, const double*,
                                                 const double*, const double*, double*, double*, double*, double*,
                                                 double*, double*, double*, double*, double*, double*, double*,
-                                                unsigned*, int*, double, int, double*, cudaStream_t);
+                                                unsigned*, int*, double, int, double*, cudaStream_t,
+                                                const GalEig<double>*);
 template cudaError_t galerkin_cg_launch<float>(int, int, int, int64_t, double, const float*, const float*,
                                                const float*, const float*, const float*, const float*, const float*,
                                                const float*, float*, float*, float*, float*, float*, float*, float*,
                                                float*, float*, float*, double*, unsigned*, int*, double, int, double*,
-                                               cudaStream_t);
+                                               cudaStream_t, const GalEig<float>*);
 
 }  // namespace cr
 

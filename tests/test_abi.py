@@ -64,7 +64,7 @@ def _desc(p, **over):
 
 
 @pytest.mark.parametrize("case", ["nan_x", "inf_y", "omega2", "lam0", "lamneg", "nonsym", "badcol", "rcap",
-                                  "mem_kind", "grid_dup", "grid_box"])
+                                  "mem_kind", "grid_dup", "grid_box", "galerkin_form"])
 def test_create_rejects_invalid_input(lib, case):
     p = synth.rect2d()
     over = {}
@@ -85,6 +85,8 @@ def test_create_rejects_invalid_input(lib, case):
         col = p.Ly.col.copy(); col[0] = p.ny + 5; over["Ly_col"] = col
     elif case == "rcap":
         opts = cr.default_options(r_cap=p.nx + 1)
+    elif case == "galerkin_form":
+        opts = cr.default_options(r_cap=4, galerkin_form=3)
     d, keep = _desc(p, **over)
     if case == "mem_kind":
         d.mem_kind = 7
