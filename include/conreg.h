@@ -250,7 +250,8 @@ void cr_destroy(struct cr_problem* p);
 cr_status cr_add_rank_one(struct cr_problem* p, cr_rank1_info* info);
 
 /* Galerkin projection (Eq. Proj_Sylv): matrix CG on Z from the current Z until
- * ‖U^T D V - K(Z)‖_F <= tol ‖U^T D V‖_F (Algorithm 1 uses tol = tau / 2). */
+ * ‖U^T D V - K(Z)‖_F <= tol ‖U^T D V‖_F (Algorithm 1 uses tol = tau / 2).  A tol
+ * below 1e-14 (0 included) asks for the rounding floor and is taken as 1e-14. */
 cr_status cr_project(struct cr_problem* p, double tol, cr_proj_info* info);
 
 /* Stopping quantities of Algorithm 1 for W = U Z V^T: relres = ‖D - A(W)‖_F/‖D‖_F
@@ -472,6 +473,18 @@ cr_status cr_net_gradients(struct cr_net* n, int32_t B, const float* in_dev, con
 /* One Adam step (beta1 0.9, beta2 0.999) on that loss; *loss_host (may be NULL) = loss before the step. */
 cr_status cr_net_train_step(struct cr_net* n, int32_t B, const float* in_dev, const float* target_dev,
                             const uint8_t* mask_dev, float lr, float* loss_host);
+
+/* Verification aid for the network kernels (no counterpart in the paper): the
+ * forward pass, the masked relative loss and the parameter gradients computed
+ * by the same kernel templates as a cr_net, instantiated with float64 storage
+ * and accumulation, on a D x H x W box (V voxels) and B samples.  All buffers
+ * are host memory: params (cr_net_param_count() values, packed as in
+ * cr_net_get_params), in (B x 2 x V), target (B x V), mask (V); outputs out
+ * (B x V), *loss and grads (packed as params).  Allocates and frees its own
+ * device memory and stream; returns after the results are copied.  EINVAL for
+ * null pointers or B * V > 2^22; ENOMEM, ECUDA. */
+cr_status cr_net_check_f64(int32_t D, int32_t H, int32_t W, int32_t B, const double* params, const double* in,
+                           const double* target, const uint8_t* mask, double* out, double* loss, double* grads);
 
 /* Voxel box of one side (0 = y grid of L_y, 1 = x grid of L_x): box_index_host[i]
  * is the linear index z*H*W + y*W + x of row i; dims = {D, H, W}. */

@@ -138,6 +138,7 @@ SIGNATURES = {
                                    C.POINTER(C.c_float), C.POINTER(C.c_float)]),
     "cr_net_train_step": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_float,
                                     C.POINTER(C.c_float)]),
+    "cr_net_check_f64": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _dp, _dp, _dp, _up, _dp, _dp, _dp]),
     "cr_set_voxel_grid": (C.c_int, [C.c_void_p, C.c_int32, _ip, _ip]),
     "cr_set_preconditioner": (C.c_int, [C.c_void_p, C.c_void_p]),
     "cr_solve_u_noalloc": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_double,
@@ -655,6 +656,25 @@ class ConvNet:
                                           mask.contiguous().data_ptr(), C.byref(loss),
                                           g.ctypes.data_as(C.POINTER(C.c_float))), None, "cr_net_gradients")
         return loss.value, g
+
+    @staticmethod
+    def check_f64(dims, params, x, target, mask):
+        """The same kernel templates in float64 (cr_net_check_f64), host arrays in and
+        out: params (float64, packed as get_params), x (B, 2, D, H, W), target
+        (B, D, H, W), mask (D, H, W) -> (out (B, D, H, W), loss, gradients)."""
+        lib = load()
+        d = list(dims) + [1] * (3 - len(dims))
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        t = np.ascontiguousarray(target, dtype=np.float64)
+        m = np.ascontiguousarray(mask, dtype=np.uint8)
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        B = x.shape[0]
+        out = np.zeros((B,) + tuple(d), dtype=np.float64)
+        grads = np.zeros(p.size, dtype=np.float64)
+        loss = C.c_double()
+        _check(lib.cr_net_check_f64(d[0], d[1], d[2], B, _ptr(p), _ptr(x), _ptr(t), _ptr(m, _up), _ptr(out),
+                                    C.byref(loss), _ptr(grads)), None, "cr_net_check_f64")
+        return out, loss.value, grads
 
     def train_step(self, x, target, mask, lr: float) -> float:
         loss = C.c_float()

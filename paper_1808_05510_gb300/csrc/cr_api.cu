@@ -208,7 +208,11 @@ struct cr_problem {
   double *eA2t = nullptr, *eB2t = nullptr, *eFt = nullptr, *eZt = nullptr, *eDen = nullptr, *eTmp = nullptr;
   double *eHt = nullptr, *eY = nullptr, *eGt = nullptr, *eg = nullptr, *eW = nullptr, *ebord = nullptr;
   double* eh = nullptr;  // pinned staging: borders, W_a, W_b, la, lb
+  // row-wise Sherman-Morrison-Woodbury preconditioner of the eigenbasis CG (m <= 128)
+  double *eDl = nullptr, *eHg = nullptr, *eCi = nullptr, *eS = nullptr, *eZz = nullptr, *eYd = nullptr;
+  bool smw_ok = false;  // set per projection when the capacitance inverses are ready
   float *fQa = nullptr, *fla = nullptr, *flb = nullptr, *fY = nullptr, *fGt = nullptr;
+  float* fZz = nullptr;
   std::vector<double> hla, hlb;
   int eq = 0;
   int64_t gal_eig_proj = 0, gal_eig_finish = 0;
@@ -1322,10 +1326,25 @@ void eig_operator(cr_problem* p) {
   gemm(j, j, j, 1.0, MatView{p->eQb, ld, 1}, MatView{p->B2, 1, ld}, 0.0, p->eTmp, 1, ld, p->ws, p->ws_elems, st);
   gemm(j, j, j, 1.0, MatView{p->eTmp, 1, ld}, MatView{p->eQb, 1, ld}, 0.0, p->eB2t, 1, ld, p->ws, p->ws_elems, st);
   gemm(j, m, j, 1.0, MatView{p->eQb, ld, 1}, MatView{p->H, 1, ld}, 0.0, p->eHt, 1, ld, p->ws, p->ws_elems, st);
-  galerkin_eig_diag(j, m, ld, p->lam, p->eA2t, p->eB2t, p->ela, p->elb, p->G, p->eHt, p->eg, p->eDen, st);
+  galerkin_eig_diag(j, m, ld, p->lam, p->eA2t, p->eB2t, p->ela, p->elb, p->G, p->eHt, p->eg, p->eDen, p->eDl,
+                    p->eHg, st);
+  p->smw_ok = false;
+  if (p->eCi) {
+    const cudaError_t e = galerkin_smw_setup(j, m, ld, p->eDl, p->eHg, p->eCi, st);
+    if (e == cudaSuccess) {
+      p->smw_ok = true;
+    } else {
+      cudaGetLastError();  // too large for the row-wise preconditioner: the diagonal one stays
+    }
+  }
 }
 
+// Relative Galerkin residual that counts as "to rounding": smaller targets (tau = 0)
+// are raised to it, so that a CG whose residual has reached the rounding floor stops.
+constexpr double kGalTolFloor = 1e-14;
+
 cr_status do_project(cr_problem* p, double tol, cr_proj_info* info) {
+  tol = std::max(tol, kGalTolFloor);
   cudaStream_t st = p->st;
   const int j = p->j;
   const int64_t ld = p->rcap;
@@ -1381,6 +1400,17 @@ cr_status do_project(cr_problem* p, double tol, cr_proj_info* info) {
     fe.lb = p->flb;
     fe.Y = p->fY;
     fe.Gt = p->fGt;
+    if (eig && p->smw_ok) {
+      fe.Dl = p->eDl;
+      fe.Hg = p->eHg;
+      fe.Ci = p->eCi;
+      fe.S = p->eS;
+      fe.Yd = p->eYd;
+      fe.Zz = p->fZz;
+    }
+    // an inner solve that has not converged by this cap hands back to the outer
+    // float64 refinement, which checks the progress itself
+    const int inner_maxit = std::min(maxit, 2000 + 10 * j);
     for (int outer = 0; outer < 40 && fn2 > 0.0; ++outer) {
       galerkin_apply(p, p->Z, p->gQ);
       mat_axpby(j, j, 1.0, p->F, ld, -1.0, p->gQ, ld, p->gR, ld, st);
@@ -1401,16 +1431,17 @@ cr_status do_project(cr_problem* p, double tol, cr_proj_info* info) {
       CUCHK(p, cudaMemsetAsync(p->fZ, 0, sizeof(float) * r2, st));
       CUCHK(p, cudaMemsetAsync(p->gbar, 0, 2 * sizeof(unsigned), st));
       CUCHK(p, cudaMemsetAsync(p->gerr, 0, sizeof(int), st));
+      // the single-cluster kernel has no row-wise preconditioner: with it, the persistent kernel
       cudaError_t ce = cudaErrorNotSupported;
-      if (!eig)
+      if (!(eig && p->smw_ok))
         ce = galerkin_cluster_f32_launch(j, p->m, ld, p->lam, p->fA1, p->fA2, p->fB1, p->fB2, p->fG, p->fH, p->fF,
-                                         p->fDg, p->fZ, 1e-7 * rr, maxit, p->gout, st);
+                                         p->fDg, p->fZ, 1e-7 * rr, inner_maxit, p->gout, st, eig ? &fe : nullptr);
       if (ce == cudaErrorNotSupported) {
         cudaGetLastError();
         ce = galerkin_cg_launch<float>(p->gal_nb, j, p->m, ld, p->lam, p->fA1, p->fA2, p->fB1, p->fB2, p->fG, p->fH,
                                        p->fF, p->fDg, p->fZ, p->fR, p->fPa, p->fPb, p->fQ, p->fT2, p->fT1, p->fTH,
-                                       p->fGw, p->fzb, p->gpart, p->gbar, p->gerr, 1e-7 * rr, maxit, p->gout, st,
-                                       eig ? &fe : nullptr);
+                                       p->fGw, p->fzb, p->gpart, p->gbar, p->gerr, 1e-7 * rr, inner_maxit, p->gout,
+                                       st, eig ? &fe : nullptr);
       }
       CUCHK(p, ce);
       double out[3] = {0, 0, 0};
@@ -1435,36 +1466,60 @@ cr_status do_project(cr_problem* p, double tol, cr_proj_info* info) {
     fn2 = p->hs->ds[DS_GS + 3];
     bool done = false;
     if (eig && fn2 > 0.0) {
-      // CG on Zt = Qa^T Z Qb from the transformed warm start, then Z = Qa Zt Qb^T
-      // and its residual in the original basis
-      eig_transform(p, p->F, p->eFt, true);
-      eig_transform(p, p->Z, p->eZt, true);
+      // CG on Zt = Qa^T Z Qb from the transformed warm start, then Z = Qa Zt Qb^T and
+      // its residual in the original basis.  Where that residual is still above the
+      // tolerance (the bases carry rounding), up to two refinement steps solve for the
+      // correction in the eigenbasis; the original-basis CG is the last resort.
       GalEig<double> ge;
       ge.Qa = p->eQa;
       ge.la = p->ela;
       ge.lb = p->elb;
       ge.Y = p->eY;
       ge.Gt = p->eGt;
-      CUCHK(p, cudaMemsetAsync(p->gbar, 0, 2 * sizeof(unsigned), st));
-      CUCHK(p, cudaMemsetAsync(p->gerr, 0, sizeof(int), st));
-      CUCHK(p, galerkin_cg_launch(p->gal_nb, j, p->m, ld, p->lam, p->A1, p->eA2t, p->B1, p->eB2t, p->G, p->eHt,
-                                  p->eFt, p->eDen, p->eZt, p->gR, p->gP, p->gT, p->gQ, p->gZB2, p->gZB1, p->gZH,
-                                  p->gGw, p->gzb, p->gpart, p->gbar, p->gerr, tol * tol * fn2, maxit, p->gout, st,
-                                  &ge));
-      double out[3] = {0, 0, 0};
-      CUCHK(p, cudaMemcpyAsync(out, p->gout, sizeof(out), cudaMemcpyDeviceToHost, st));
-      p->d2h_bytes += (int64_t)sizeof(out);
-      TRY(sync(p));
-      k = (int)out[0];
-      if (out[2] == 3.0) return fail(p, CR_ETIMEOUT, "Galerkin CG grid barrier timed out");
-      eig_transform(p, p->eZt, p->Z, false);
-      galerkin_apply(p, p->Z, p->gQ);
-      mat_axpby(j, j, 1.0, p->F, ld, -1.0, p->gQ, ld, p->gR, ld, st);
-      mat_dot(j, j, p->gR, ld, p->gR, ld, gs + 4, st);
-      TRY(readback(p, DS_GS + 4, 1, false));
-      rr = p->hs->ds[DS_GS + 4];
+      if (p->smw_ok) {
+        ge.Dl = p->eDl;
+        ge.Hg = p->eHg;
+        ge.Ci = p->eCi;
+        ge.S = p->eS;
+        ge.Yd = p->eYd;
+        ge.Zz = p->eZz;
+      }
       ++p->gal_eig_proj;
-      done = rr <= tol * tol * fn2;
+      for (int ref = 0; ref < 3 && !done; ++ref) {
+        if (ref == 0) {
+          eig_transform(p, p->F, p->eFt, true);
+          eig_transform(p, p->Z, p->eZt, true);
+        } else {
+          eig_transform(p, p->gR, p->eFt, true);
+          fill(ld * ld, 0.0, p->eZt, st);
+        }
+        CUCHK(p, cudaMemsetAsync(p->gbar, 0, 2 * sizeof(unsigned), st));
+        CUCHK(p, cudaMemsetAsync(p->gerr, 0, sizeof(int), st));
+        // the whole system to the tolerance itself (a tighter first target costs more
+        // iterations than the refinements it saves); a correction to half of it
+        const double t2 = (ref == 0 ? 1.0 : 0.25) * tol * tol * fn2;
+        CUCHK(p, galerkin_cg_launch(p->gal_nb, j, p->m, ld, p->lam, p->A1, p->eA2t, p->B1, p->eB2t, p->G, p->eHt,
+                                    p->eFt, p->eDen, p->eZt, p->gR, p->gP, p->gT, p->gQ, p->gZB2, p->gZB1, p->gZH,
+                                    p->gGw, p->gzb, p->gpart, p->gbar, p->gerr, t2, std::max(1, maxit - k), p->gout,
+                                    st, &ge));
+        double out[3] = {0, 0, 0};
+        CUCHK(p, cudaMemcpyAsync(out, p->gout, sizeof(out), cudaMemcpyDeviceToHost, st));
+        p->d2h_bytes += (int64_t)sizeof(out);
+        TRY(sync(p));
+        k += (int)out[0];
+        if (out[2] == 3.0) return fail(p, CR_ETIMEOUT, "Galerkin CG grid barrier timed out");
+        eig_transform(p, p->eZt, p->Z, false, ref == 0 ? 0.0 : 1.0);
+        galerkin_apply(p, p->Z, p->gQ);
+        mat_axpby(j, j, 1.0, p->F, ld, -1.0, p->gQ, ld, p->gR, ld, st);
+        mat_dot(j, j, p->gR, ld, p->gR, ld, gs + 4, st);
+        TRY(readback(p, DS_GS + 4, 1, false));
+        rr = p->hs->ds[DS_GS + 4];
+        done = rr <= tol * tol * fn2;
+        if (!done && k >= maxit) {  // the cap covers every CG of the projection
+          done = true;
+          rc = fail(p, CR_ENOTCONV, "Galerkin CG reached its iteration cap");
+        }
+      }
       if (!done) ++p->gal_eig_finish;
     }
     if (fn2 > 0.0 && !done) {
@@ -1472,7 +1527,7 @@ cr_status do_project(cr_problem* p, double tol, cr_proj_info* info) {
       CUCHK(p, cudaMemsetAsync(p->gerr, 0, sizeof(int), st));
       CUCHK(p, galerkin_cg_launch(p->gal_nb, j, p->m, ld, p->lam, p->A1, p->A2, p->B1, p->B2, p->G, p->H, p->F,
                                   p->gDg, p->Z, p->gR, p->gP, p->gT, p->gQ, p->gZB2, p->gZB1, p->gZH, p->gGw, p->gzb,
-                                  p->gpart, p->gbar, p->gerr, tol * tol * fn2, maxit, p->gout, st));
+                                  p->gpart, p->gbar, p->gerr, tol * tol * fn2, maxit - k, p->gout, st));
       double out[3] = {0, 0, 0};
       CUCHK(p, cudaMemcpyAsync(out, p->gout, sizeof(out), cudaMemcpyDeviceToHost, st));
       p->d2h_bytes += (int64_t)sizeof(out);
@@ -2023,6 +2078,9 @@ cr_status cr_create(const cr_problem_desc* d_in, const cr_options* o, cr_problem
     for (double** b : {&p->eHt, &p->eY, &p->eGt}) CK(dalloc(p, b, (size_t)rc * m));
     for (double** b : {&p->ela, &p->elb}) CK(dalloc(p, b, rc));
     CK(dalloc(p, &p->eg, m));
+    for (double** b : {&p->eDl, &p->eZz, &p->eYd}) CK(dalloc(p, b, r2));
+    for (double** b : {&p->eHg, &p->eS}) CK(dalloc(p, b, (size_t)rc * m));
+    if (m <= 128) CK(dalloc(p, &p->eCi, (size_t)rc * m * m));
     CK(dalloc(p, &p->eW, 2 * r2));
     CK(dalloc(p, &p->ebord, 2 * ((size_t)rc + 1)));
     if (cudaMallocHost(&p->eh, sizeof(double) * (2 * ((size_t)rc + 1) + 2 * r2 + 2 * (size_t)rc)) != cudaSuccess) {
@@ -2032,7 +2090,7 @@ cr_status cr_create(const cr_problem_desc* d_in, const cr_options* o, cr_problem
       return abort_create(CR_ENOMEM);
     }
     if (opt.precision == CR_MIXED) {
-      CK(dalloc(p, &p->fQa, r2));
+      for (float** b : {&p->fQa, &p->fZz}) CK(dalloc(p, b, r2));
       for (float** b : {&p->fla, &p->flb}) CK(dalloc(p, b, rc));
       for (float** b : {&p->fY, &p->fGt}) CK(dalloc(p, b, (size_t)rc * m));
     }

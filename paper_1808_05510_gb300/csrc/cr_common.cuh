@@ -268,17 +268,29 @@ int galerkin_grid_size();
 // Eigenbasis form of the Galerkin CG: Qa (j x j, ld) the eigenvectors of A1,
 // la, lb the eigenvalues of A1 and B1; Y, Gt ld x m work.  The launch's A2, B2,
 // H, F, Z and Dg are then the transformed A2t, B2t, Ht, Ft, Zt and diagonal.
+// With Ci set (m <= 128), the CG is preconditioned row by row by Sherman-Morrison-
+// Woodbury (Dl, Hg, Ci from galerkin_eig_diag and galerkin_smw_setup, float64 in
+// both instantiations; S ld x m and Yd j x j float64 work, Zz j x j work);
+// otherwise by the diagonal Dg.
 template <class T>
 struct GalEig {
   const T *Qa = nullptr, *la = nullptr, *lb = nullptr;
   T *Y = nullptr, *Gt = nullptr;
+  const double *Dl = nullptr, *Hg = nullptr, *Ci = nullptr;
+  double *S = nullptr, *Yd = nullptr;
+  T* Zz = nullptr;
 };
 // Diagonal of the eigenbasis Galerkin operator with each G_a replaced by its mean
 // diagonal g_a = tr(G_a) / j (g: m doubles, written):
-//   Den(i, k) = lam (A2t_ii + 2 la_i lb_k + B2t_kk) + sum_a g_a Ht(k, a)^2
+//   Dl(i, k) = lam (A2t_ii + 2 la_i lb_k + B2t_kk),  Den = Dl + sum_a g_a Ht(k, a)^2,
+//   Hg = Ht diag(sqrt g)  (ld x m)
 void galerkin_eig_diag(int j, int m, int64_t ld, double lam, const double* A2t, const double* B2t, const double* la,
-                       const double* lb, const double* G, const double* Ht, double* g, double* Den,
-                       cudaStream_t st);
+                       const double* lb, const double* G, const double* Ht, double* g, double* Den, double* Dl,
+                       double* Hg, cudaStream_t st);
+// Ci: j blocks of m x m, C_i^-1 with C_i = I + Hg^T diag(1 / Dl(i, :)) Hg.
+// cudaErrorNotSupported for m > 128.
+cudaError_t galerkin_smw_setup(int j, int m, int64_t ld, const double* Dl, const double* Hg, double* Ci,
+                               cudaStream_t st);
 // T = double (float64 form) or float (inner solve of the mixed form); eig = nullptr: original basis
 template <class T>
 cudaError_t galerkin_cg_launch(int nb, int j, int m, int64_t ld, double lam, const T* A1, const T* A2, const T* B1,
@@ -290,10 +302,11 @@ cudaError_t galerkin_cg_launch(int nb, int j, int m, int64_t ld, double lam, con
 // Single-cluster float32 Galerkin CG (inner solves of the mixed form, j <= 128,
 // m <= 128); cudaErrorNotSupported when the sizes do not fit.  Solves
 // K32 Z = F from Z = 0 until |F - K32 Z|^2 <= tol2.  out: iterations, |R|^2, status.
+// eig != nullptr: the eigenbasis form (Qa, la, lb used; A2, B2, H, Dg transformed).
 cudaError_t galerkin_cluster_f32_launch(int j, int m, int64_t ld, double lam, const float* A1, const float* A2,
                                         const float* B1, const float* B2, const float* G, const float* H,
                                         const float* F, const float* Dg, float* Z, double tol2, int maxit,
-                                        double* out, cudaStream_t st);
+                                        double* out, cudaStream_t st, const GalEig<float>* eig = nullptr);
 
 // ---------------------------------------------------------------- cr_net.cu / cr_fcg.cu
 cudaError_t net_apply(cr_net* n, const float* in, float* out, cudaStream_t st);

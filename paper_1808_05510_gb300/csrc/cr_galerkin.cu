@@ -24,7 +24,15 @@
 //   B' Gt = Qa^T Gw
 //   C  Q = lam T2 + 2 lam la_i lb_l X + lam A2t X + Gt Ht^T
 // Dg then holds the diagonal of Kt with the data term's G_a replaced by its mean
-// diagonal (an SPD preconditioner; the iterate it converges to is the same).
+// diagonal g_a (an SPD preconditioner; the iterate it converges to is the same).
+// With that replacement the data term of row i of Kt is Zt(i, :) Hg Hg^T
+// (Hg = Ht diag(sqrt g), rank m), so row i of the operator's "diagonal part" is
+// D_i + Hg Hg^T with D_i = diag(Dl(i, :)): the row-wise Sherman-Morrison-Woodbury
+// preconditioner inverts exactly that (m x m capacitance matrix C_i per row,
+// inverted once per projection) at the cost of two thin products per iteration:
+//   D  ... R -= alpha Q; y = R ./ Dl
+//   S  S(i, :) = C_i^-1 (y(i, :) Hg)           (one CTA per row)
+//   Z  z = y - (S Hg^T) ./ Dl, <R, z>, <R, R>    (8x8 tiles)
 // Tiles use all CTAs; each output is summed in a fixed order (k split in four
 // fixed ranges added in order), and every CTA adds the per-CTA partial sums of
 // the inner products in block order, so all CTAs take the same decisions and
@@ -59,6 +67,13 @@ struct GalArgs {
   // eigenbasis form (Qa == nullptr: the original basis); A1, B1 unused there
   const T *Qa, *la, *lb;
   T *Yb, *Gt;  // ld x m work
+  // row-wise Sherman-Morrison-Woodbury preconditioner (Ci == nullptr: z = R ./ Dg):
+  //   row i of z = D_i^-1 r_i - D_i^-1 Hg C_i^-1 Hg^T D_i^-1 r_i,  D_i = Dl(i, :)
+  // kept in float64 in both instantiations: where the data term dominates a row, the
+  // correction cancels most of D_i^-1 r_i, which float32 would not resolve
+  const double *Dl, *Hg, *Ci;  // j x j (ld), ld x m, j blocks of m x m
+  double *Sb, *Yd;             // ld x m, j x j (ld) work
+  T* Zz;                       // j x j (ld) work
 };
 
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
@@ -150,10 +165,18 @@ __device__ void grid_total(const GalArgs<T>& a, double (&out)[NV]) {
 
 // One 8x8 output tile of sum_k A(i, k) B(k, l); 256 threads = 64 outputs x 4
 // k-groups.  Returns this thread's partial; combine with tile_reduce.
+// Staging tiles of tile_term: one buffer per element type, shared by every
+// instantiation (each lambda pair would otherwise declare its own arrays).
+template <class T>
+__device__ __forceinline__ T (*tile_buf())[TS + 1] {
+  __shared__ T buf[64][TS + 1];
+  return buf;
+}
+
 template <class T, class GA, class GB>
 __device__ __forceinline__ T tile_term(int i0, int l0, int M, int N, int K, GA ga, GB gb, T acc) {
-  __shared__ T As[32][TS + 1];
-  __shared__ T Bs[32][TS + 1];
+  T(*As)[TS + 1] = tile_buf<T>();
+  T(*Bs)[TS + 1] = As + 32;
   const int tid = threadIdx.x;
   const int o = tid & 63, g = tid >> 6;
   const int oi = o & 7, ol = o >> 3;
@@ -308,6 +331,63 @@ __device__ bool apply_K(const GalArgs<T>& a, const T* X, double& pq) {
   return true;
 }
 
+// Row-wise SMW preconditioner, after y = R ./ Dl has been stored in Yz (and a grid
+// barrier): S(i, :) = C_i^-1 (y_i Hg) per row, then z = y - (S Hg^T) ./ Dl into Zo
+// with this CTA's partials of <R, z> and <R, R> in v.
+template <class T>
+__device__ bool precond_smw(const GalArgs<T>& a, const double* Yz, T* Zo, double (&v)[2]) {
+  const int j = a.j, m = a.m;
+  const int64_t ld = a.ld;
+  __shared__ double wpart[8][128];
+  __shared__ double wrow[128];
+  const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;  // 8 groups of 32
+  const int kc = (j + 7) / 8, k0 = min(j, grp * kc), k1 = min(j, k0 + kc);
+  for (int i = blockIdx.x; i < j; i += a.nb) {
+    for (int al = lane; al < m; al += 32) {
+      double s = 0.0;
+      for (int k = k0; k < k1; ++k) s = fma(ldcg(Yz + i + k * ld), a.Hg[k + al * ld], s);
+      wpart[grp][al] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < m) {
+      double s = 0.0;
+#pragma unroll
+      for (int g = 0; g < 8; ++g) s += wpart[g][threadIdx.x];
+      wrow[threadIdx.x] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < m) {
+      const double* c = a.Ci + ((int64_t)i * m + threadIdx.x) * m;
+      double s = 0.0;
+      for (int b = 0; b < m; ++b) s = fma(c[b], wrow[b], s);
+      a.Sb[i + threadIdx.x * ld] = s;
+    }
+    __syncthreads();
+  }
+  if (!grid_barrier(a)) return false;
+  const int nt = (j + TS - 1) / TS;
+  v[0] = v[1] = 0.0;
+  for (int it = blockIdx.x; it < nt * nt; it += a.nb) {
+    const int ti = it % nt, tl = it / nt;
+    double acc = tile_term<double>(ti * TS, tl * TS, j, j, m, [&](int i, int k) { return ldcg(a.Sb + i + k * ld); },
+                                   [&](int k, int l) { return a.Hg[l + k * ld]; }, 0.0);
+    bool ok;
+    const double r = tile_reduce<double>(acc, ok);
+    if (ok) {
+      const int i = ti * TS + (threadIdx.x & 7), l = tl * TS + (threadIdx.x >> 3);
+      if (i < j && l < j) {
+        const int64_t o = i + l * ld;
+        const T z = (T)(ldcg(Yz + o) - r / a.Dl[o]);
+        const T rv = ldcg(a.R + o);
+        Zo[o] = z;
+        v[0] += (double)rv * (double)z;
+        v[1] += (double)rv * (double)rv;
+      }
+    }
+  }
+  return true;
+}
+
 template <class T>
 __global__ void __launch_bounds__(kGThreads, 1) galerkin_cg_kernel(const GalArgs<T> a) {
   const int j = a.j;
@@ -321,7 +401,18 @@ __global__ void __launch_bounds__(kGThreads, 1) galerkin_cg_kernel(const GalArgs
   double pq;
   if (!apply_K(a, a.Z, pq)) goto timeout;
   if (!grid_barrier(a)) goto timeout;
-  {
+  if (a.Ci) {
+    for (int64_t t = e0 + threadIdx.x; t < e1; t += blockDim.x) {
+      const int64_t o = (t % j) + (t / j) * ld;
+      const T r = a.F[o] - ldcg(a.Q + o);
+      a.R[o] = r;
+      a.Yd[o] = (double)r / a.Dl[o];
+    }
+    if (!grid_barrier(a)) goto timeout;
+    double v[2];
+    if (!precond_smw(a, a.Yd, a.Pa, v)) goto timeout;
+    cta_partial<2>(v, a);
+  } else {
     double v[2] = {0.0, 0.0};
     for (int64_t t = e0 + threadIdx.x; t < e1; t += blockDim.x) {
       const int64_t o = (t % j) + (t / j) * ld;
@@ -362,7 +453,19 @@ __global__ void __launch_bounds__(kGThreads, 1) galerkin_cg_kernel(const GalArgs
         break;
       }
       const T alpha = (T)(rho / pqt[0]);
-      {
+      if (a.Ci) {
+        for (int64_t t = e0 + threadIdx.x; t < e1; t += blockDim.x) {
+          const int64_t o = (t % j) + (t / j) * ld;
+          a.Z[o] = fma(alpha, ldcg(X + o), a.Z[o]);
+          const T r = fma(-alpha, ldcg(a.Q + o), a.R[o]);
+          a.R[o] = r;
+          a.Yd[o] = (double)r / a.Dl[o];
+        }
+        if (!grid_barrier(a)) goto timeout;
+        double v[2];
+        if (!precond_smw(a, a.Yd, a.Zz, v)) goto timeout;
+        cta_partial<2>(v, a);
+      } else {
         double v[2] = {0.0, 0.0};
         for (int64_t t = e0 + threadIdx.x; t < e1; t += blockDim.x) {
           const int64_t o = (t % j) + (t / j) * ld;
@@ -385,7 +488,7 @@ __global__ void __launch_bounds__(kGThreads, 1) galerkin_cg_kernel(const GalArgs
       ++k;
       for (int64_t t = e0 + threadIdx.x; t < e1; t += blockDim.x) {
         const int64_t o = (t % j) + (t / j) * ld;
-        Xn[o] = fma(beta, ldcg(X + o), a.zb[o]);
+        Xn[o] = fma(beta, ldcg(X + o), a.Ci ? ldcg(a.Zz + o) : a.zb[o]);
       }
       if (!grid_barrier(a)) goto timeout;
       T* tmp = X;
@@ -426,11 +529,13 @@ __global__ void gal_trace_kernel(int j, int64_t ld, const double* __restrict__ G
   }
 }
 
-// Den(i, k) = lam (A2t_ii + 2 la_i lb_k + B2t_kk) + sum_a g_a Ht(k, a)^2
+// Dl(i, k) = lam (A2t_ii + 2 la_i lb_k + B2t_kk), Den = Dl + sum_a g_a Ht(k, a)^2,
+// and (first column of threads) Hg(k, a) = sqrt(g_a) Ht(k, a)
 __global__ void gal_eig_den_kernel(int j, int m, int64_t ld, double lam, const double* __restrict__ A2t,
                                    const double* __restrict__ B2t, const double* __restrict__ la,
                                    const double* __restrict__ lb, const double* __restrict__ g,
-                                   const double* __restrict__ Ht, double* __restrict__ Den) {
+                                   const double* __restrict__ Ht, double* __restrict__ Den, double* __restrict__ Dl,
+                                   double* __restrict__ Hg) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)j * j) return;
   const int i = (int)(t % j), k = (int)(t / j);
@@ -438,16 +543,59 @@ __global__ void gal_eig_den_kernel(int j, int m, int64_t ld, double lam, const d
   for (int a = 0; a < m; ++a) {
     const double x = Ht[k + (int64_t)a * ld];
     h = fma(g[a] * x, x, h);
+    if (i == 0) Hg[k + (int64_t)a * ld] = sqrt(fmax(g[a], 0.0)) * x;
   }
   const double li = fmax(la[i], 0.0), lk = fmax(lb[k], 0.0);  // A1, B1 are positive semidefinite
-  Den[i + (int64_t)k * ld] =
-      lam * (A2t[i + (int64_t)i * ld] + 2.0 * li * lk + B2t[k + (int64_t)k * ld]) + h;
+  const double dl = lam * (A2t[i + (int64_t)i * ld] + 2.0 * li * lk + B2t[k + (int64_t)k * ld]);
+  Dl[i + (int64_t)k * ld] = dl;
+  Den[i + (int64_t)k * ld] = dl + h;
+}
+
+// C_i = I + Hg^T diag(1 / Dl(i, :)) Hg (m x m, SPD with eigenvalues >= 1), inverted in
+// shared memory by Gauss-Jordan elimination without pivoting; one CTA per row i.
+__global__ void gal_smw_setup_kernel(int j, int m, int64_t ld, const double* __restrict__ Dl,
+                                     const double* __restrict__ Hg, double* __restrict__ Ci) {
+  extern __shared__ double sm[];
+  double* C = sm;              // m x m, row-major
+  double* prow = C + m * m;    // scaled pivot row
+  double* fcol = prow + m;     // pivot column
+  double* dinv = fcol + m;     // 1 / Dl(i, :)
+  const int i = blockIdx.x;
+  for (int k = threadIdx.x; k < j; k += blockDim.x) dinv[k] = 1.0 / Dl[i + (int64_t)k * ld];
+  __syncthreads();
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+    const int r = t / m, c = t % m;
+    if (c < r) continue;
+    const double* hr = Hg + (int64_t)r * ld;
+    const double* hc = Hg + (int64_t)c * ld;
+    double s = 0.0;
+    for (int k = 0; k < j; ++k) s = fma(hr[k] * dinv[k], hc[k], s);
+    s += r == c ? 1.0 : 0.0;
+    C[r * m + c] = s;
+    C[c * m + r] = s;
+  }
+  for (int p = 0; p < m; ++p) {
+    __syncthreads();
+    const double piv = 1.0 / C[p * m + p];
+    for (int t = threadIdx.x; t < m; t += blockDim.x) {
+      prow[t] = (t == p ? 1.0 : C[p * m + t]) * piv;
+      fcol[t] = C[t * m + p];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+      const int r = t / m, c = t % m;
+      C[t] = r == p ? prow[c] : (c == p ? 0.0 : C[t]) - fcol[r] * prow[c];
+    }
+  }
+  __syncthreads();
+  double* out = Ci + (int64_t)i * m * m;
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) out[t] = C[t];
 }
 }  // namespace
 
 void galerkin_eig_diag(int j, int m, int64_t ld, double lam, const double* A2t, const double* B2t, const double* la,
-                       const double* lb, const double* G, const double* Ht, double* g, double* Den,
-                       cudaStream_t st) {
+                       const double* lb, const double* G, const double* Ht, double* g, double* Den, double* Dl,
+                       double* Hg, cudaStream_t st) {
   if (j <= 0) return;
   if (m > 0) {
     count_launch();
@@ -455,7 +603,24 @@ void galerkin_eig_diag(int j, int m, int64_t ld, double lam, const double* A2t, 
   }
   const int64_t tot = (int64_t)j * j;
   count_launch();
-  gal_eig_den_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(j, m, ld, lam, A2t, B2t, la, lb, g, Ht, Den);
+  gal_eig_den_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(j, m, ld, lam, A2t, B2t, la, lb, g, Ht, Den,
+                                                                       Dl, Hg);
+}
+
+size_t galerkin_smw_smem(int j, int m) { return sizeof(double) * ((size_t)m * m + 2 * (size_t)m + (size_t)j); }
+
+cudaError_t galerkin_smw_setup(int j, int m, int64_t ld, const double* Dl, const double* Hg, double* Ci,
+                               cudaStream_t st) {
+  if (j <= 0 || m <= 0) return cudaSuccess;
+  if (m > 128) return cudaErrorNotSupported;
+  const size_t smem = galerkin_smw_smem(j, m);
+  if (smem > 227 * 1024) return cudaErrorNotSupported;
+  cudaError_t e = cudaFuncSetAttribute(gal_smw_setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  count_launch();
+  gal_smw_setup_kernel<<<j, 256, smem, st>>>(j, m, ld, Dl, Hg, Ci);
+  return cudaGetLastError();
 }
 
 int galerkin_grid_size() {
@@ -482,6 +647,14 @@ cudaError_t galerkin_cg_launch(int nb, int j, int m, int64_t ld, double lam, con
     a.lb = eig->lb;
     a.Yb = eig->Y;
     a.Gt = eig->Gt;
+    if (eig->Ci && m <= 128) {
+      a.Dl = eig->Dl;
+      a.Hg = eig->Hg;
+      a.Ci = eig->Ci;
+      a.Sb = eig->S;
+      a.Yd = eig->Yd;
+      a.Zz = eig->Zz;
+    }
   }
   a.j = j;
   a.m = m;
@@ -533,7 +706,9 @@ template cudaError_t galerkin_cg_launch<float>(int, int, int, int64_t, double, c
 
 // ---------------------------------------------------------------------------
 // Single-cluster float32 Galerkin CG for the inner solves of the mixed form
-// (j <= 128, m <= 128).  The columns of the CG matrices are split over the
+// (j <= 128, m <= 128), in the original basis or the eigenbasis form (then
+// TH(:, own a) goes through Y = Qa TH before G_a and the result through Qa^T,
+// both local to the CTA that owns a, and the A1 X B1 term is a scaling).  The columns of the CG matrices are split over the
 // CTAs of one cluster; every CTA keeps a full copy of the current search
 // direction X and of Gw = [G_a X h_a]_a in shared memory, refreshed by an
 // all-gather over distributed shared memory, so every product is local:
@@ -559,6 +734,7 @@ struct GalClArgs {
   int64_t ld;
   float lam;
   const float *A1, *A2, *B1, *B2, *G, *H, *F, *Dg;
+  const float *Qa, *la, *lb;  // eigenbasis form (Qa == nullptr: the original basis)
   float* Z;
   float tol2;  // stop when |R|^2 <= tol2
   int maxit;
@@ -625,12 +801,14 @@ __global__ void __launch_bounds__(kClThreads, 1) galerkin_cluster_f32_kernel(con
   float* T2o = T1o + j * cw;
   float* Dio = T2o + j * cw;       // 1 / diag(K) on own columns
   float* THo = Dio + j * cw;       // j x aw
-  DF* scr = reinterpret_cast<DF*>(THo + j * aw);  // [32]
+  float* Yo = THo + j * aw;        // j x aw (eigenbasis form: Qa TH)
+  DF* scr = reinterpret_cast<DF*>(Yo + j * aw);  // [32]
   DF* red = scr + 32;              // [4]
   float* scal = reinterpret_cast<float*>(red + 4);  // [8]
   float* Uo = Xf + (int64_t)c0 * j;  // own columns of U inside the full copy
   const int tid = threadIdx.x, nth = blockDim.x;
   const float lam = a.lam, lam2 = 2.f * a.lam;
+  const bool eig = a.Qa != nullptr;
 
   // Z = 0, R = F, U = D^-1 R
   for (int t = tid; t < j * nc; t += nth) {
@@ -650,18 +828,28 @@ __global__ void __launch_bounds__(kClThreads, 1) galerkin_cluster_f32_kernel(con
     cl.sync();  // B1: own columns of U published
     gather_blocks(cl, Xf, j * j, j * cw, rank);
     __syncthreads();
-    for (int t = tid; t < j * nc; t += nth) {
-      const int i = t % j, lc = t / j;
-      const float* b2 = a.B2 + (int64_t)(c0 + lc) * ld;
-      const float* b1 = a.B1 + (int64_t)(c0 + lc) * ld;
-      float s2 = 0.f, s1 = 0.f;
-      for (int k = 0; k < j; ++k) {
-        const float x = Xf[i + k * j];
-        s2 = fmaf(x, __ldg(b2 + k), s2);
-        s1 = fmaf(x, __ldg(b1 + k), s1);
+    if (eig) {
+      for (int t = tid; t < j * nc; t += nth) {
+        const int i = t % j, lc = t / j;
+        const float* b2 = a.B2 + (int64_t)(c0 + lc) * ld;
+        float s2 = 0.f;
+        for (int k = 0; k < j; ++k) s2 = fmaf(Xf[i + k * j], __ldg(b2 + k), s2);
+        T2o[t] = s2;
       }
-      T2o[t] = s2;
-      T1o[t] = s1;
+    } else {
+      for (int t = tid; t < j * nc; t += nth) {
+        const int i = t % j, lc = t / j;
+        const float* b2 = a.B2 + (int64_t)(c0 + lc) * ld;
+        const float* b1 = a.B1 + (int64_t)(c0 + lc) * ld;
+        float s2 = 0.f, s1 = 0.f;
+        for (int k = 0; k < j; ++k) {
+          const float x = Xf[i + k * j];
+          s2 = fmaf(x, __ldg(b2 + k), s2);
+          s1 = fmaf(x, __ldg(b1 + k), s1);
+        }
+        T2o[t] = s2;
+        T1o[t] = s1;
+      }
     }
     for (int t = tid; t < j * na; t += nth) {
       const int i = t % j, la = t / j;
@@ -671,12 +859,37 @@ __global__ void __launch_bounds__(kClThreads, 1) galerkin_cluster_f32_kernel(con
       THo[t] = s;
     }
     __syncthreads();
+    if (eig) {  // Y = Qa TH on own injections
+      for (int t = tid; t < j * na; t += nth) {
+        const int i = t % j, la = t / j;
+        float s = 0.f;
+        for (int k = 0; k < j; ++k) s = fmaf(__ldg(a.Qa + i + (int64_t)k * ld), THo[k + la * j], s);
+        Yo[t] = s;
+      }
+      __syncthreads();
+    }
+    const float* src = eig ? Yo : THo;
     for (int t = tid; t < j * na; t += nth) {
       const int i = t % j, la = t / j;
       const float* g = a.G + (int64_t)(a0 + la) * ld * ld;
       float s = 0.f;
-      for (int q = 0; q < j; ++q) s = fmaf(__ldg(g + i + (int64_t)q * ld), THo[q + la * j], s);
+      for (int q = 0; q < j; ++q) s = fmaf(__ldg(g + i + (int64_t)q * ld), src[q + la * j], s);
       Gwf[i + (a0 + la) * j] = s;
+    }
+    if (eig) {  // Gw <- Qa^T Gw on own injections (through TH)
+      __syncthreads();
+      for (int t = tid; t < j * na; t += nth) {
+        const int i = t % j, la = t / j;
+        const float* q = a.Qa + (int64_t)i * ld;
+        float s = 0.f;
+        for (int k = 0; k < j; ++k) s = fmaf(__ldg(q + k), Gwf[k + (a0 + la) * j], s);
+        THo[t] = s;
+      }
+      __syncthreads();
+      for (int t = tid; t < j * na; t += nth) {
+        const int i = t % j, la = t / j;
+        Gwf[i + (a0 + la) * j] = THo[t];
+      }
     }
     cl.sync();  // B2: own columns of Gw published
     gather_blocks(cl, Gwf, j * m, j * aw, rank);
@@ -687,9 +900,14 @@ __global__ void __launch_bounds__(kClThreads, 1) galerkin_cluster_f32_kernel(con
       const int i = t % j, lc = t / j;
       const int l = c0 + lc;
       float s1 = 0.f, s2 = 0.f, s3 = 0.f;
-      for (int k = 0; k < j; ++k) {
-        s1 = fmaf(__ldg(a.A1 + i + (int64_t)k * ld), T1o[k + lc * j], s1);
-        s2 = fmaf(__ldg(a.A2 + i + (int64_t)k * ld), Uo[k + lc * j], s2);
+      if (eig) {
+        for (int k = 0; k < j; ++k) s2 = fmaf(__ldg(a.A2 + i + (int64_t)k * ld), Uo[k + lc * j], s2);
+        s1 = __ldg(a.la + i) * __ldg(a.lb + l) * Uo[t];
+      } else {
+        for (int k = 0; k < j; ++k) {
+          s1 = fmaf(__ldg(a.A1 + i + (int64_t)k * ld), T1o[k + lc * j], s1);
+          s2 = fmaf(__ldg(a.A2 + i + (int64_t)k * ld), Uo[k + lc * j], s2);
+        }
       }
       for (int al = 0; al < m; ++al) s3 = fmaf(Gwf[i + al * j], __ldg(a.H + l + (int64_t)al * ld), s3);
       const float w = lam * T2o[t] + lam2 * s1 + lam * s2 + s3;
@@ -786,8 +1004,8 @@ __global__ void __launch_bounds__(kClThreads, 1) galerkin_cluster_f32_kernel(con
 }
 
 size_t gal_cl_smem(int j, int m, int cw, int aw) {
-  return sizeof(float) * ((size_t)j * j + (size_t)j * m + 9 * (size_t)j * cw + (size_t)j * aw) + sizeof(DF) * 40 +
-         sizeof(float) * 8 + 64;
+  return sizeof(float) * ((size_t)j * j + (size_t)j * m + 9 * (size_t)j * cw + 2 * (size_t)j * aw) +
+         sizeof(DF) * 40 + sizeof(float) * 8 + 64;
 }
 
 }  // namespace
@@ -797,7 +1015,7 @@ size_t gal_cl_smem(int j, int m, int cw, int aw) {
 cudaError_t galerkin_cluster_f32_launch(int j, int m, int64_t ld, double lam, const float* A1, const float* A2,
                                         const float* B1, const float* B2, const float* G, const float* H,
                                         const float* F, const float* Dg, float* Z, double tol2, int maxit,
-                                        double* out, cudaStream_t st) {
+                                        double* out, cudaStream_t st, const GalEig<float>* eig) {
   if (j < 1 || j > 128 || m > 128) return cudaErrorNotSupported;
   const int C = std::min(kClMax, j);
   const int cw = (j + C - 1) / C, aw = (m + C - 1) / C;
@@ -823,6 +1041,11 @@ cudaError_t galerkin_cluster_f32_launch(int j, int m, int64_t ld, double lam, co
   a.H = H;
   a.F = F;
   a.Dg = Dg;
+  if (eig) {
+    a.Qa = eig->Qa;
+    a.la = eig->la;
+    a.lb = eig->lb;
+  }
   a.Z = Z;
   a.tol2 = (float)tol2;
   a.maxit = maxit;

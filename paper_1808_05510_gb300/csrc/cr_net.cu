@@ -42,114 +42,146 @@ __device__ __forceinline__ bool nb(const Dims& g, int z, int y, int x, int t, in
   return true;
 }
 
+// Storage type S (bf16 on the solver path, double in the float64 check) and
+// accumulation type A (float, double).
+__device__ __forceinline__ float to_acc(bf16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ double to_acc(double v) { return v; }
+template <class S>
+__device__ __forceinline__ S from_acc(float v);
+template <>
+__device__ __forceinline__ bf16 from_acc<bf16>(float v) {
+  return __float2bfloat16_rn(v);
+}
+template <class S>
+__device__ __forceinline__ S from_acc(double v) {
+  return v;
+}
+__device__ __forceinline__ float fmax0(float v) { return fmaxf(v, 0.f); }
+__device__ __forceinline__ double fmax0(double v) { return fmax(v, 0.0); }
+
+// Weights as A: staged in shared memory for float accumulation, read from
+// global memory in the float64 check (a 16 x 16 x 27 double block exceeds the
+// static shared-memory limit).
 // out[b, co, v] = act(bias[co] + sum_ci sum_t W[co, ci, t] in[b, ci, v + t])
-template <int CI, int CO, bool RELU, bool OUTF32>
-__global__ void __launch_bounds__(kThreads) conv_fwd(Dims g, int B, const bf16* __restrict__ in,
-                                                     const bf16* __restrict__ Wb, const float* __restrict__ bias,
+template <int CI, int CO, bool RELU, bool OUTA, class S, class A>
+__global__ void __launch_bounds__(kThreads) conv_fwd(Dims g, int B, const S* __restrict__ in,
+                                                     const S* __restrict__ Wb, const A* __restrict__ bias,
                                                      void* out) {
-  __shared__ float Ws[CO * CI * 27];
-  for (int i = threadIdx.x; i < CO * CI * 27; i += blockDim.x) Ws[i] = __bfloat162float(Wb[i]);
-  __syncthreads();
+  __shared__ float Wsf[sizeof(A) == 4 ? CO * CI * 27 : 1];
+  const A* Ws;
+  if constexpr (sizeof(A) == 4) {
+    for (int i = threadIdx.x; i < CO * CI * 27; i += blockDim.x) Wsf[i] = to_acc(Wb[i]);
+    __syncthreads();
+    Ws = reinterpret_cast<const A*>(Wsf);
+  } else {
+    Ws = reinterpret_cast<const A*>(Wb);
+  }
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)B * g.V) return;
   const int b = (int)(t / g.V);
   const int64_t v = t % g.V;
   const int x = (int)(v % g.W), y = (int)((v / g.W) % g.H), z = (int)(v / ((int64_t)g.W * g.H));
-  float acc[CO];
+  A acc[CO];
 #pragma unroll
   for (int co = 0; co < CO; ++co) acc[co] = bias[co];
-  const bf16* ib = in + (int64_t)b * CI * g.V;
+  const S* ib = in + (int64_t)b * CI * g.V;
   for (int tap = 0; tap < 27; ++tap) {
     int64_t off;
     if (!nb(g, z, y, x, tap, off)) continue;
 #pragma unroll
     for (int ci = 0; ci < CI; ++ci) {
-      const float a = __bfloat162float(ib[(int64_t)ci * g.V + off]);
+      const A a = to_acc(ib[(int64_t)ci * g.V + off]);
 #pragma unroll
-      for (int co = 0; co < CO; ++co) acc[co] = fmaf(Ws[(co * CI + ci) * 27 + tap], a, acc[co]);
+      for (int co = 0; co < CO; ++co) acc[co] = fma(Ws[(co * CI + ci) * 27 + tap], a, acc[co]);
     }
   }
 #pragma unroll
   for (int co = 0; co < CO; ++co) {
-    const float r = RELU ? fmaxf(acc[co], 0.f) : acc[co];
-    if (OUTF32)
-      ((float*)out)[((int64_t)b * CO + co) * g.V + v] = r;
+    const A r = RELU ? fmax0(acc[co]) : acc[co];
+    if (OUTA)
+      ((A*)out)[((int64_t)b * CO + co) * g.V + v] = r;
     else
-      ((bf16*)out)[((int64_t)b * CO + co) * g.V + v] = __float2bfloat16_rn(r);
+      ((S*)out)[((int64_t)b * CO + co) * g.V + v] = from_acc<S>(r);
   }
 }
 
 // gin[b, ci, u] = relu'(a_in[b, ci, u]) * sum_co sum_t W[co, ci, t] gout[b, co, u - t]
-template <int CI, int CO>
-__global__ void __launch_bounds__(kThreads) conv_bwd_data(Dims g, int B, const float* __restrict__ gout,
-                                                          const bf16* __restrict__ Wb, const bf16* __restrict__ ain,
-                                                          float* __restrict__ gin) {
-  __shared__ float Ws[CO * CI * 27];
-  for (int i = threadIdx.x; i < CO * CI * 27; i += blockDim.x) Ws[i] = __bfloat162float(Wb[i]);
-  __syncthreads();
+template <int CI, int CO, class S, class A>
+__global__ void __launch_bounds__(kThreads) conv_bwd_data(Dims g, int B, const A* __restrict__ gout,
+                                                          const S* __restrict__ Wb, const S* __restrict__ ain,
+                                                          A* __restrict__ gin) {
+  __shared__ float Wsf[sizeof(A) == 4 ? CO * CI * 27 : 1];
+  const A* Ws;
+  if constexpr (sizeof(A) == 4) {
+    for (int i = threadIdx.x; i < CO * CI * 27; i += blockDim.x) Wsf[i] = to_acc(Wb[i]);
+    __syncthreads();
+    Ws = reinterpret_cast<const A*>(Wsf);
+  } else {
+    Ws = reinterpret_cast<const A*>(Wb);
+  }
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)B * g.V) return;
   const int b = (int)(t / g.V);
   const int64_t u = t % g.V;
   const int x = (int)(u % g.W), y = (int)((u / g.W) % g.H), z = (int)(u / ((int64_t)g.W * g.H));
-  float acc[CI];
+  A acc[CI];
 #pragma unroll
-  for (int ci = 0; ci < CI; ++ci) acc[ci] = 0.f;
-  const float* gb = gout + (int64_t)b * CO * g.V;
+  for (int ci = 0; ci < CI; ++ci) acc[ci] = (A)0;
+  const A* gb = gout + (int64_t)b * CO * g.V;
   for (int tap = 0; tap < 27; ++tap) {
     int64_t off;
     if (!nb(g, z, y, x, 26 - tap, off)) continue;  // v = u - t  <=>  tap mirrored
 #pragma unroll
     for (int co = 0; co < CO; ++co) {
-      const float gv = gb[(int64_t)co * g.V + off];
+      const A gv = gb[(int64_t)co * g.V + off];
 #pragma unroll
-      for (int ci = 0; ci < CI; ++ci) acc[ci] = fmaf(Ws[(co * CI + ci) * 27 + tap], gv, acc[ci]);
+      for (int ci = 0; ci < CI; ++ci) acc[ci] = fma(Ws[(co * CI + ci) * 27 + tap], gv, acc[ci]);
     }
   }
 #pragma unroll
   for (int ci = 0; ci < CI; ++ci) {
     const int64_t o = ((int64_t)b * CI + ci) * g.V + u;
-    gin[o] = __bfloat162float(ain[o]) > 0.f ? acc[ci] : 0.f;
+    gin[o] = to_acc(ain[o]) > (A)0 ? acc[ci] : (A)0;
   }
 }
 
 // dW[co, ci, t] = sum_b sum_v gout[b, co, v] a_in[b, ci, v + t]; db[co] = sum_b sum_v gout[b, co, v]
 // one block per (co, ci); fixed-order block reduction
-template <int CI, int CO>
-__global__ void __launch_bounds__(kThreads) conv_bwd_weight(Dims g, int B, const float* __restrict__ gout,
-                                                            const bf16* __restrict__ ain, float* __restrict__ dW,
-                                                            float* __restrict__ db) {
+template <int CI, int CO, class S, class A>
+__global__ void __launch_bounds__(kThreads) conv_bwd_weight(Dims g, int B, const A* __restrict__ gout,
+                                                            const S* __restrict__ ain, A* __restrict__ dW,
+                                                            A* __restrict__ db) {
   const int co = blockIdx.x / CI, ci = blockIdx.x % CI;
-  float acc[28];
+  A acc[28];
 #pragma unroll
-  for (int k = 0; k < 28; ++k) acc[k] = 0.f;
+  for (int k = 0; k < 28; ++k) acc[k] = (A)0;
   const int64_t tot = (int64_t)B * g.V;
   for (int64_t t = threadIdx.x; t < tot; t += blockDim.x) {
     const int b = (int)(t / g.V);
     const int64_t v = t % g.V;
-    const float gv = gout[((int64_t)b * CO + co) * g.V + v];
-    if (gv == 0.f) continue;
+    const A gv = gout[((int64_t)b * CO + co) * g.V + v];
+    if (gv == (A)0) continue;
     const int x = (int)(v % g.W), y = (int)((v / g.W) % g.H), z = (int)(v / ((int64_t)g.W * g.H));
-    const bf16* ab = ain + ((int64_t)b * CI + ci) * g.V;
+    const S* ab = ain + ((int64_t)b * CI + ci) * g.V;
 #pragma unroll
     for (int tap = 0; tap < 27; ++tap) {
       int64_t off;
-      if (nb(g, z, y, x, tap, off)) acc[tap] = fmaf(gv, __bfloat162float(ab[off]), acc[tap]);
+      if (nb(g, z, y, x, tap, off)) acc[tap] = fma(gv, to_acc(ab[off]), acc[tap]);
     }
     acc[27] += gv;
   }
-  __shared__ float red[kThreads / 32][28];
+  __shared__ A red[kThreads / 32][28];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < 28; ++k) {
-    float s = acc[k];
+    A s = acc[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (lane == 0) red[wid][k] = s;
   }
   __syncthreads();
   if (threadIdx.x < 28) {
-    float s = 0.f;
+    A s = (A)0;
     for (int w = 0; w < kThreads / 32; ++w) s += red[w][threadIdx.x];
     if (threadIdx.x < 27)
       dW[(co * CI + ci) * 27 + threadIdx.x] = s;
@@ -164,17 +196,18 @@ __global__ void to_bf16_kernel(int64_t n, const float* __restrict__ x, bf16* __r
 }
 
 // partial sums of num = sum m (o - t)^2, den = sum m t^2 over blocks (fixed order)
-__global__ void loss_partial_kernel(int64_t V, int B, const float* __restrict__ out, const float* __restrict__ tgt,
-                                    const uint8_t* __restrict__ mask, float* __restrict__ part) {
-  float a = 0.f, c = 0.f;
+template <class A>
+__global__ void loss_partial_kernel(int64_t V, int B, const A* __restrict__ out, const A* __restrict__ tgt,
+                                    const uint8_t* __restrict__ mask, A* __restrict__ part) {
+  A a = (A)0, c = (A)0;
   const int64_t tot = (int64_t)B * V;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
     if (!mask[t % V]) continue;
-    const float d = out[t] - tgt[t];
-    a = fmaf(d, d, a);
-    c = fmaf(tgt[t], tgt[t], c);
+    const A d = out[t] - tgt[t];
+    a = fma(d, d, a);
+    c = fma(tgt[t], tgt[t], c);
   }
-  __shared__ float red[2][kThreads / 32];
+  __shared__ A red[2][kThreads / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -187,7 +220,7 @@ __global__ void loss_partial_kernel(int64_t V, int B, const float* __restrict__ 
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    float s0 = 0.f, s1 = 0.f;
+    A s0 = (A)0, s1 = (A)0;
     for (int w = 0; w < kThreads / 32; ++w) {
       s0 += red[0][w];
       s1 += red[1][w];
@@ -197,26 +230,28 @@ __global__ void loss_partial_kernel(int64_t V, int B, const float* __restrict__ 
   }
 }
 
-__global__ void loss_final_kernel(int nb, const float* __restrict__ part, float* __restrict__ res) {
+template <class A>
+__global__ void loss_final_kernel(int nb, const A* __restrict__ part, A* __restrict__ res) {
   if (threadIdx.x == 0) {
-    float a = 0.f, c = 0.f;
+    A a = (A)0, c = (A)0;
     for (int b = 0; b < nb; ++b) {
       a += part[2 * b];
       c += part[2 * b + 1];
     }
     res[0] = a;
     res[1] = c;
-    res[2] = c > 0.f ? a / c : 0.f;
+    res[2] = c > (A)0 ? a / c : (A)0;
   }
 }
 
 // g = 2 m (o - t) / den
-__global__ void loss_grad_kernel(int64_t V, int B, const float* __restrict__ out, const float* __restrict__ tgt,
-                                 const uint8_t* __restrict__ mask, const float* __restrict__ res, float* __restrict__ g) {
+template <class A>
+__global__ void loss_grad_kernel(int64_t V, int B, const A* __restrict__ out, const A* __restrict__ tgt,
+                                 const uint8_t* __restrict__ mask, const A* __restrict__ res, A* __restrict__ g) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)B * V) return;
-  const float den = res[1];
-  g[t] = (mask[t % V] && den > 0.f) ? 2.f * (out[t] - tgt[t]) / den : 0.f;
+  const A den = res[1];
+  g[t] = (mask[t % V] && den > (A)0) ? (A)2 * (out[t] - tgt[t]) / den : (A)0;
 }
 
 __global__ void adam_kernel(int64_t n, float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
@@ -268,45 +303,79 @@ bool net_alloc(cr_net* n, T** p, size_t count) {
   return true;
 }
 
-void launch_fwd(cr_net* n, int B) {
-  const Dims g = n->g;
+// The network's device buffers for one instantiation (S storage, A accumulation).
+template <class S, class A>
+struct NetBufs {
+  const S* Wb[kL];
+  const A* b[kL];
+  S* act[kL];    // act[0] = input (B x 2 x V), act[l] = output of layer l (l = 1..3)
+  A* out;        // B x V
+  A *g0, *g1;    // gradient ping-pong (B x 16 x V)
+  A *part, *res;
+  A *gW[kL], *gb[kL];
+};
+
+template <class S, class A>
+void launch_fwd(const NetBufs<S, A>& n, const Dims& g, int B, cudaStream_t st) {
   const unsigned grid = nblk((int64_t)B * g.V);
   cr::count_launch();
-  conv_fwd<2, 16, true, false><<<grid, kThreads, 0, n->st>>>(g, B, n->act[0], n->Wb[0], n->b[0], n->act[1]);
+  conv_fwd<2, 16, true, false, S, A><<<grid, kThreads, 0, st>>>(g, B, n.act[0], n.Wb[0], n.b[0], n.act[1]);
   cr::count_launch();
-  conv_fwd<16, 16, true, false><<<grid, kThreads, 0, n->st>>>(g, B, n->act[1], n->Wb[1], n->b[1], n->act[2]);
+  conv_fwd<16, 16, true, false, S, A><<<grid, kThreads, 0, st>>>(g, B, n.act[1], n.Wb[1], n.b[1], n.act[2]);
   cr::count_launch();
-  conv_fwd<16, 16, true, false><<<grid, kThreads, 0, n->st>>>(g, B, n->act[2], n->Wb[2], n->b[2], n->act[3]);
+  conv_fwd<16, 16, true, false, S, A><<<grid, kThreads, 0, st>>>(g, B, n.act[2], n.Wb[2], n.b[2], n.act[3]);
   cr::count_launch();
-  conv_fwd<16, 1, false, true><<<grid, kThreads, 0, n->st>>>(g, B, n->act[3], n->Wb[3], n->b[3], n->out);
+  conv_fwd<16, 1, false, true, S, A><<<grid, kThreads, 0, st>>>(g, B, n.act[3], n.Wb[3], n.b[3], n.out);
 }
 
 // loss + gradients of all parameters into gW/gb for the batch in act[0]/out
-void launch_bwd(cr_net* n, int B, const float* tgt, const uint8_t* mask) {
-  const Dims g = n->g;
+template <class S, class A>
+void launch_bwd(const NetBufs<S, A>& n, const Dims& g, int B, const A* tgt, const uint8_t* mask, cudaStream_t st) {
   const unsigned grid = nblk((int64_t)B * g.V);
   const int nbp = 128;
   cr::count_launch();
-  loss_partial_kernel<<<nbp, kThreads, 0, n->st>>>(g.V, B, n->out, tgt, mask, n->part);
+  loss_partial_kernel<A><<<nbp, kThreads, 0, st>>>(g.V, B, n.out, tgt, mask, n.part);
   cr::count_launch();
-  loss_final_kernel<<<1, 32, 0, n->st>>>(nbp, n->part, n->res);
+  loss_final_kernel<A><<<1, 32, 0, st>>>(nbp, n.part, n.res);
   cr::count_launch();
-  loss_grad_kernel<<<grid, kThreads, 0, n->st>>>(g.V, B, n->out, tgt, mask, n->res, n->g0);
+  loss_grad_kernel<A><<<grid, kThreads, 0, st>>>(g.V, B, n.out, tgt, mask, n.res, n.g0);
   // layer 3 (16 -> 1, linear): g0 = dloss/dz_3
   cr::count_launch();
-  conv_bwd_weight<16, 1><<<16, kThreads, 0, n->st>>>(g, B, n->g0, n->act[3], n->gW[3], n->gb[3]);
+  conv_bwd_weight<16, 1, S, A><<<16, kThreads, 0, st>>>(g, B, n.g0, n.act[3], n.gW[3], n.gb[3]);
   cr::count_launch();
-  conv_bwd_data<16, 1><<<grid, kThreads, 0, n->st>>>(g, B, n->g0, n->Wb[3], n->act[3], n->g1);
+  conv_bwd_data<16, 1, S, A><<<grid, kThreads, 0, st>>>(g, B, n.g0, n.Wb[3], n.act[3], n.g1);
   cr::count_launch();
-  conv_bwd_weight<16, 16><<<256, kThreads, 0, n->st>>>(g, B, n->g1, n->act[2], n->gW[2], n->gb[2]);
+  conv_bwd_weight<16, 16, S, A><<<256, kThreads, 0, st>>>(g, B, n.g1, n.act[2], n.gW[2], n.gb[2]);
   cr::count_launch();
-  conv_bwd_data<16, 16><<<grid, kThreads, 0, n->st>>>(g, B, n->g1, n->Wb[2], n->act[2], n->g0);
+  conv_bwd_data<16, 16, S, A><<<grid, kThreads, 0, st>>>(g, B, n.g1, n.Wb[2], n.act[2], n.g0);
   cr::count_launch();
-  conv_bwd_weight<16, 16><<<256, kThreads, 0, n->st>>>(g, B, n->g0, n->act[1], n->gW[1], n->gb[1]);
+  conv_bwd_weight<16, 16, S, A><<<256, kThreads, 0, st>>>(g, B, n.g0, n.act[1], n.gW[1], n.gb[1]);
   cr::count_launch();
-  conv_bwd_data<16, 16><<<grid, kThreads, 0, n->st>>>(g, B, n->g0, n->Wb[1], n->act[1], n->g1);
+  conv_bwd_data<16, 16, S, A><<<grid, kThreads, 0, st>>>(g, B, n.g0, n.Wb[1], n.act[1], n.g1);
   cr::count_launch();
-  conv_bwd_weight<2, 16><<<32, kThreads, 0, n->st>>>(g, B, n->g1, n->act[0], n->gW[0], n->gb[0]);
+  conv_bwd_weight<2, 16, S, A><<<32, kThreads, 0, st>>>(g, B, n.g1, n.act[0], n.gW[0], n.gb[0]);
+}
+
+NetBufs<bf16, float> bufs(const cr_net* n) {
+  NetBufs<bf16, float> b{};
+  for (int l = 0; l < kL; ++l) {
+    b.Wb[l] = n->Wb[l];
+    b.b[l] = n->b[l];
+    b.act[l] = n->act[l];
+    b.gW[l] = n->gW[l];
+    b.gb[l] = n->gb[l];
+  }
+  b.out = n->out;
+  b.g0 = n->g0;
+  b.g1 = n->g1;
+  b.part = n->part;
+  b.res = n->res;
+  return b;
+}
+
+void launch_fwd(cr_net* n, int B) { launch_fwd(bufs(n), n->g, B, n->st); }
+void launch_bwd(cr_net* n, int B, const float* tgt, const uint8_t* mask) {
+  launch_bwd(bufs(n), n->g, B, tgt, mask, n->st);
 }
 
 void refresh_bf16(cr_net* n) {
@@ -473,6 +542,88 @@ cr_status cr_net_train_step(cr_net* n, int32_t B, const float* in_dev, const flo
     *loss_host = res[2];
   }
   return cudaGetLastError() == cudaSuccess ? CR_OK : CR_ECUDA;
+}
+
+cr_status cr_net_check_f64(int32_t D, int32_t H, int32_t W, int32_t B, const double* params, const double* in,
+                           const double* target, const uint8_t* mask, double* out, double* loss, double* grads) {
+  if (D < 1 || H < 1 || W < 1 || B < 1 || (int64_t)D * H * W * B > (1ll << 22) || !params || !in || !target ||
+      !mask || !out || !loss || !grads) {
+    cr::set_global_error("cr_net_check_f64: bad arguments");
+    return CR_EINVAL;
+  }
+  const Dims g{D, H, W, (int64_t)D * H * W};
+  const int64_t V = g.V;
+  // one device block: parameters and gradients, activations, output, work
+  const int64_t np = cr_net_param_count();
+  int64_t nact = 0;
+  for (int l = 0; l < kL; ++l) nact += (int64_t)B * kCh[l] * V;
+  const int64_t total = 2 * np + nact + (int64_t)B * V * 2 + 2 * (int64_t)B * 16 * V + 256 + 4;
+  double* blk = nullptr;
+  uint8_t* dmask = nullptr;
+  cudaStream_t st = nullptr;
+  cr_status rc = CR_OK;
+  if (cudaMalloc(&blk, sizeof(double) * total) != cudaSuccess || cudaMalloc(&dmask, V) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    cr::set_global_error("cr_net_check_f64: device allocation failed");
+    rc = CR_ENOMEM;
+  } else {
+    NetBufs<double, double> b{};
+    double* q = blk;
+    double* P = q;  // parameters, packed as in cr_net_get_params
+    q += np;
+    double* Gp = q;  // gradients, same packing
+    q += np;
+    {
+      double *p = P, *gp = Gp;
+      for (int l = 0; l < kL; ++l) {
+        b.Wb[l] = p;
+        b.gW[l] = gp;
+        p += wcount(l);
+        gp += wcount(l);
+        b.b[l] = p;
+        b.gb[l] = gp;
+        p += kCh[l + 1];
+        gp += kCh[l + 1];
+      }
+    }
+    for (int l = 0; l < kL; ++l) {
+      b.act[l] = q;
+      q += (int64_t)B * kCh[l] * V;
+    }
+    b.out = q;
+    q += (int64_t)B * V;
+    double* tg = q;
+    q += (int64_t)B * V;
+    b.g0 = q;
+    q += (int64_t)B * 16 * V;
+    b.g1 = q;
+    q += (int64_t)B * 16 * V;
+    b.part = q;
+    q += 256;
+    b.res = q;
+    cudaMemsetAsync(blk, 0, sizeof(double) * total, st);
+    cudaMemcpyAsync(P, params, sizeof(double) * np, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(b.act[0], in, sizeof(double) * B * 2 * V, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(tg, target, sizeof(double) * B * V, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(dmask, mask, V, cudaMemcpyHostToDevice, st);
+    launch_fwd(b, g, B, st);
+    launch_bwd(b, g, B, tg, dmask, st);
+    double res[3] = {0, 0, 0};
+    cudaMemcpyAsync(out, b.out, sizeof(double) * B * V, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(grads, Gp, sizeof(double) * np, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(res, b.res, sizeof(res), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+      cr::set_global_error("cr_net_check_f64: CUDA error");
+      rc = CR_ECUDA;
+    } else {
+      *loss = res[2];
+    }
+  }
+  if (st) cudaStreamDestroy(st);
+  if (blk) cudaFree(blk);
+  if (dmask) cudaFree(dmask);
+  return rc;
 }
 
 }  // extern "C"

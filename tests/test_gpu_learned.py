@@ -1,10 +1,16 @@
 """Learned preconditioner: the network kernels against the float64 oracle
 (oracle/conv3d.py), training on the GPU, and the gain over Jacobi-PCG.
 
-Stated error: the GPU network stores weights and activations in BF16 and
-accumulates in float32, so against the float64 oracle (fed the same
-BF16-rounded weights and inputs) the output agrees to 3e-2 and the parameter
-gradients to 5e-2 (relative, Frobenius) on a 4 x 5 x 6 box."""
+Stated errors (relative, Frobenius, 4 x 5 x 6 box, 2 samples):
+- the same kernel templates instantiated with float64 storage and
+  accumulation (cr_net_check_f64): output, loss and gradients to 1e-10;
+- the BF16 network (BF16 weights and activations, float32 accumulation)
+  against the oracle run with the same BF16 storage (weights, input and every
+  hidden activation rounded to BF16 as the kernels store them): 1e-2;
+- the BF16 network against the exact float64 network (only weights and input
+  rounded): 3e-2 for the output, 5e-2 for the gradients.  That gap is the BF16
+  storage of the hidden activations (8 significant bits, about 4e-3 per value,
+  compounded over four layers of 27 x 16 taps), not the kernels."""
 import numpy as np
 import pytest
 
@@ -73,6 +79,70 @@ def test_network_forward_and_gradients_match_oracle(env):
         assert np.linalg.norm(gW[l] - dWs[l]) <= 5e-2 * np.linalg.norm(dWs[l]), l
         assert np.linalg.norm(gb[l] - dbs[l]) <= 5e-2 * np.linalg.norm(dbs[l]) + 1e-7, l
     net.close()
+
+
+def random_case(cr, seed, dims=(4, 5, 6), B=2):
+    rng = np.random.default_rng(seed)
+    flat = 0.25 * rng.standard_normal(cr.ConvNet.param_count())
+    x = rng.standard_normal((B, 2) + dims)
+    t = rng.standard_normal((B,) + dims)
+    mask = (rng.random(dims) > 0.25).astype(np.uint8)
+    return flat, x, t, mask
+
+
+def oracle_all(x, Ws, bs, t, mask, round_fn=None):
+    """Oracle forward, loss and gradients; round_fn (if given) is applied to the
+    input and to every hidden activation, as the network's storage does."""
+    r = round_fn or (lambda a: a)
+    acts = [r(x)]
+    for l in range(4):
+        z = conv3d.conv(acts[-1], Ws[l], bs[l])
+        acts.append(r(np.maximum(z, 0.0)) if l < 3 else z)
+    loss, gout = conv3d.loss_and_grad_out(acts[-1], t[:, None], mask.astype(np.float64))
+    dWs, dbs = conv3d.backward(acts, Ws, gout)
+    return acts[-1][:, 0], loss, dWs, dbs
+
+
+def test_float64_template_matches_oracle(env):
+    """cr_net_check_f64 runs the network's own kernel templates in float64."""
+    torch, cr = env
+    flat, x, t, mask = random_case(cr, 8)
+    out, loss, g = cr.ConvNet.check_f64((4, 5, 6), flat, x, t, mask)
+    Ws, bs = unpack(flat)
+    ref, loss_ref, dWs, dbs = oracle_all(x, Ws, bs, t, mask)
+    assert np.linalg.norm(out - ref) <= 1e-10 * np.linalg.norm(ref)
+    assert abs(loss - loss_ref) <= 1e-10 * loss_ref
+    gW, gb = unpack(g)
+    for l in range(4):
+        assert np.linalg.norm(gW[l] - dWs[l]) <= 1e-10 * np.linalg.norm(dWs[l]), l
+        assert np.linalg.norm(gb[l] - dbs[l]) <= 1e-10 * np.linalg.norm(dbs[l]), l
+
+
+def test_bf16_network_matches_oracle_with_bf16_storage(env):
+    torch, cr = env
+    dims = (4, 5, 6)
+    flat, x, t, mask = random_case(cr, 9)
+    flat = flat.astype(np.float32)
+    net = cr.ConvNet(dims, batch_cap=2, seed=3)
+    net.set_params(flat)
+    dev = torch.device("cuda")
+    xd = torch.tensor(x.astype(np.float32), device=dev)
+    td = torch.tensor(t.astype(np.float32), device=dev)
+    md = torch.tensor(mask, device=dev)
+    out = net.forward(xd).cpu().numpy().astype(np.float64)
+    loss, g = net.gradients(xd, td, md)
+    net.close()
+    Ws, bs = unpack(flat)
+    Ws = [bf16(w, torch) for w in Ws]
+    r = lambda a: bf16(a, torch)  # noqa: E731
+    ref, loss_ref, dWs, dbs = oracle_all(x.astype(np.float32).astype(np.float64), Ws, bs,
+                                         t.astype(np.float32).astype(np.float64), mask, round_fn=r)
+    assert np.linalg.norm(out - ref) <= 1e-2 * np.linalg.norm(ref)
+    assert abs(loss - loss_ref) <= 1e-2 * loss_ref
+    gW, gb = unpack(g)
+    for l in range(4):
+        assert np.linalg.norm(gW[l] - dWs[l]) <= 1e-2 * np.linalg.norm(dWs[l]), l
+        assert np.linalg.norm(gb[l] - dbs[l]) <= 1e-2 * np.linalg.norm(dbs[l]) + 1e-7, l
 
 
 def test_untrained_network_is_jacobi(env):
