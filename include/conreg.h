@@ -203,6 +203,7 @@ typedef enum {
   CR_PHASE_GALERKIN = 4, /* Galerkin CG on Eq. (Proj_Sylv) and the masked data residual */
   CR_PHASE_RESID = 5,    /* residual norm, objective, dW */
   CR_PHASE_PCG_KERNEL = 6, /* the Jacobi-PCG kernel launches alone (inside PCG_U / PCG_V) */
+  CR_PHASE_BASIS = 7,    /* eigenbasis updates of the Galerkin CG's eigenbasis form (inside GALERKIN) */
   CR_NPHASE = 8
 } cr_phase;
 
@@ -222,7 +223,6 @@ typedef struct {
   int64_t pcg_multigrid[2];       /* levels of the multigrid preconditioner per side (0 = not in use) */
   int64_t galerkin_eigen[2];      /* projections solved in the eigenbasis form (0), of which the
                                      original-basis CG had to finish (1) */
-  double galerkin_basis_ms;       /* host time spent on the eigenbasis updates (arrowhead steps) */
 } cr_stats;
 
 /* Fill *o with defaults (struct_size set).  Always succeeds for o != NULL. */
@@ -473,6 +473,14 @@ cr_status cr_net_gradients(struct cr_net* n, int32_t B, const float* in_dev, con
 /* One Adam step (beta1 0.9, beta2 0.999) on that loss; *loss_host (may be NULL) = loss before the step. */
 cr_status cr_net_train_step(struct cr_net* n, int32_t B, const float* in_dev, const float* target_dev,
                             const uint8_t* mask_dev, float lr, float* loss_host);
+
+/* Verification aid for the Galerkin CG's eigenbasis updates (no counterpart in
+ * the paper): the device arrowhead eigen-decomposition of [diag(d) z; z^T alpha]
+ * (d: n values, ascending), on host buffers: mu (n + 1, ascending) and W
+ * ((n + 1)^2, column-major, columns the eigenvectors in the order of mu).
+ * Allocates and frees its own device memory and stream; returns after the
+ * results are copied.  EINVAL for n < 0, n > 4096 or null pointers. */
+cr_status cr_arrow_check(int32_t n, const double* d, const double* z, double alpha, double* mu, double* W);
 
 /* Verification aid for the network kernels (no counterpart in the paper): the
  * forward pass, the masked relative loss and the parameter gradients computed

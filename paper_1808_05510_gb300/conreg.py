@@ -73,7 +73,7 @@ class cr_proj_info(C.Structure):
     _fields_ = [("iters", C.c_int32), ("relres", C.c_double)]
 
 
-PHASES = ["pcg_u", "pcg_v", "rhs", "orth", "galerkin", "resid", "pcg_kernel", "p7"]
+PHASES = ["pcg_u", "pcg_v", "rhs", "orth", "galerkin", "resid", "pcg_kernel", "basis"]
 
 
 class cr_stats(C.Structure):
@@ -81,8 +81,7 @@ class cr_stats(C.Structure):
                 ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("phase_ms", C.c_double * 8), ("phase_calls", C.c_int64 * 8),
                 ("learned_solves", C.c_int64), ("learned_fallbacks", C.c_int64), ("learned_off", C.c_int64),
                 ("mixed_handovers", C.c_int64), ("pcg_cluster", C.c_int64 * 2),
-                ("pcg_multigrid", C.c_int64 * 2), ("galerkin_eigen", C.c_int64 * 2),
-                ("galerkin_basis_ms", C.c_double)]
+                ("pcg_multigrid", C.c_int64 * 2), ("galerkin_eigen", C.c_int64 * 2)]
 
 
 class cr_solve_info(C.Structure):
@@ -138,6 +137,7 @@ SIGNATURES = {
                                    C.POINTER(C.c_float), C.POINTER(C.c_float)]),
     "cr_net_train_step": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_float,
                                     C.POINTER(C.c_float)]),
+    "cr_arrow_check": (C.c_int, [C.c_int32, _dp, _dp, C.c_double, _dp, _dp]),
     "cr_net_check_f64": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _dp, _dp, _dp, _up, _dp, _dp, _dp]),
     "cr_set_voxel_grid": (C.c_int, [C.c_void_p, C.c_int32, _ip, _ip]),
     "cr_set_preconditioner": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -497,8 +497,7 @@ class ConReg:
                 "learned_off": s.learned_off, "mixed_handovers": s.mixed_handovers,
                 "pcg_cluster": [s.pcg_cluster[0], s.pcg_cluster[1]],
                 "pcg_multigrid": [s.pcg_multigrid[0], s.pcg_multigrid[1]],
-                "galerkin_eigen": [s.galerkin_eigen[0], s.galerkin_eigen[1]],
-                "galerkin_basis_ms": s.galerkin_basis_ms}
+                "galerkin_eigen": [s.galerkin_eigen[0], s.galerkin_eigen[1]]}
 
     def cr_solve_u(self, v, rhs, allow_notconv: bool = False):
         """(solution, iterations); with ``allow_notconv`` a solve that stopped at
@@ -592,6 +591,19 @@ def solve_batch(p, members, r_max: int, tau: float = 0.0, relres_target: float =
 
 def cr_lambda_from_bar(lam_bar: float, ninj: int, nx: int) -> float:
     return load().cr_lambda_from_bar(float(lam_bar), int(ninj), int(nx))
+
+
+def arrow_check(d, z, alpha):
+    """The device arrowhead eigen-decomposition (cr_arrow_check): (mu, W)."""
+    lib = load()
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    n = d.size
+    mu = np.zeros(n + 1)
+    W = np.zeros((n + 1, n + 1), order="F")
+    _check(lib.cr_arrow_check(n, _ptr(d), _ptr(z), float(alpha), _ptr(mu), W.ctypes.data_as(_dp)), None,
+           "cr_arrow_check")
+    return mu, W
 
 
 class ConvNet:

@@ -27,13 +27,11 @@
 #include <cmath>
 #include <cstring>
 #include <string>
-#include <thread>
 #include <tuple>
 #include <vector>
 
 #include "conreg.h"
 #include "cr_common.cuh"
-#include "cr_host_arrow.h"
 #include "cr_host_linalg.h"
 #include "cr_mg_host.h"
 
@@ -207,16 +205,14 @@ struct cr_problem {
   double *eQa = nullptr, *eQa2 = nullptr, *eQb = nullptr, *eQb2 = nullptr, *ela = nullptr, *elb = nullptr;
   double *eA2t = nullptr, *eB2t = nullptr, *eFt = nullptr, *eZt = nullptr, *eDen = nullptr, *eTmp = nullptr;
   double *eHt = nullptr, *eY = nullptr, *eGt = nullptr, *eg = nullptr, *eW = nullptr, *ebord = nullptr;
-  double* eh = nullptr;  // pinned staging: borders, W_a, W_b, la, lb
+  double* earw = nullptr;  // arrowhead work, both sides
   // row-wise Sherman-Morrison-Woodbury preconditioner of the eigenbasis CG (m <= 128)
   double *eDl = nullptr, *eHg = nullptr, *eCi = nullptr, *eS = nullptr, *eZz = nullptr, *eYd = nullptr;
   bool smw_ok = false;  // set per projection when the capacitance inverses are ready
   float *fQa = nullptr, *fla = nullptr, *flb = nullptr, *fY = nullptr, *fGt = nullptr;
   float* fZz = nullptr;
-  std::vector<double> hla, hlb;
   int eq = 0;
   int64_t gal_eig_proj = 0, gal_eig_finish = 0;
-  double gal_basis_ms = 0.0;
   // float32 copies for the mixed form's inner Galerkin CG
   // learned preconditioner: box index of each row per side, the network, its buffers
   int* box[2] = {nullptr, nullptr};
@@ -1234,56 +1230,41 @@ cr_status mixed_G(cr_problem* p, bool tensor_cores = false) {
 // rank one border at a time.  With A1 = Qa diag(la) Qa^T, the bordered matrix
 // [A1 a; a^T alpha] equals blockdiag(Qa, 1) M blockdiag(Qa, 1)^T for the
 // arrowhead M of (la, Qa^T a, alpha); with M = W diag(mu) W^T the new basis is
-// blockdiag(Qa, 1) W and the new eigenvalues mu.  The arrowhead step runs on the
-// host (cr_host::arrow_eig, O(q^2)); the product with W on the device.
+// blockdiag(Qa, 1) W and the new eigenvalues mu.  Everything runs on the device
+// (arrow_update, then one product per side), with no host round trip.
 cr_status eig_sync(cr_problem* p) {
   cudaStream_t st = p->st;
   const int64_t ld = p->rcap;
   const int j = p->j;
   if (p->eq >= j) return CR_OK;
-  const auto t0 = std::chrono::steady_clock::now();
-  double* hb = p->eh;                         // borders: a side at [0, ld + 1), b side after
-  double* hW = hb + 2 * (ld + 1);             // W_a, then W_b (each (q+1)^2, column-major)
-  double* hl = hW + 2 * ld * ld;              // la, lb
-  std::vector<double> mua, mub, Wa, Wb;
+  prof_begin(p, CR_PHASE_BASIS);
   while (p->eq < j) {
     const int q = p->eq, n1 = q + 1;
     fill(1, 1.0, p->eQa + q + q * ld, st);   // blockdiag(Qa, 1): the rest of row and column q is zero
     fill(1, 1.0, p->eQb + q + q * ld, st);
+    double* za = p->ebord;
+    double* zb = p->ebord + ld + 1;
     if (q > 0) {
-      gemv_t(q, q, p->eQa, ld, p->A1 + q * ld, p->ebord, 1, 1.0, 0.0, st);
-      gemv_t(q, q, p->eQb, ld, p->B1 + q * ld, p->ebord + ld + 1, 1, 1.0, 0.0, st);
+      gemv_t(q, q, p->eQa, ld, p->A1 + q * ld, za, 1, 1.0, 0.0, st);
+      gemv_t(q, q, p->eQb, ld, p->B1 + q * ld, zb, 1, 1.0, 0.0, st);
     }
-    copy(1, p->A1 + q + q * ld, p->ebord + q, st);
-    copy(1, p->B1 + q + q * ld, p->ebord + ld + 1 + q, st);
-    CUCHK(p, cudaMemcpyAsync(hb, p->ebord, sizeof(double) * 2 * (ld + 1), cudaMemcpyDeviceToHost, st));
-    p->d2h_bytes += (int64_t)sizeof(double) * 2 * (ld + 1);
-    TRY(sync(p));
-    const std::vector<double> za(hb, hb + q), zb(hb + ld + 1, hb + ld + 1 + q);
-    std::thread tb([&]() { cr_host::arrow_eig(q, p->hlb, zb, hb[ld + 1 + q], mub, Wb); });
-    cr_host::arrow_eig(q, p->hla, za, hb[q], mua, Wa);
-    tb.join();
-    std::copy(Wa.begin(), Wa.end(), hW);
-    std::copy(Wb.begin(), Wb.end(), hW + (size_t)n1 * n1);
-    CUCHK(p, cudaMemcpyAsync(p->eW, hW, sizeof(double) * 2 * n1 * n1, cudaMemcpyHostToDevice, st));
-    p->h2d_bytes += (int64_t)sizeof(double) * 2 * n1 * n1;
-    gemm(n1, n1, n1, 1.0, MatView{p->eQa, 1, ld}, MatView{p->eW, 1, n1}, 0.0, p->eQa2, 1, ld, p->ws, p->ws_elems,
+    copy(1, p->A1 + q + q * ld, za + q, st);
+    copy(1, p->B1 + q + q * ld, zb + q, st);
+    const double* d[2] = {p->ela, p->elb};
+    const double* z[2] = {za, zb};
+    const double* al[2] = {za + q, zb + q};
+    double* mu[2] = {p->ela, p->elb};
+    double* W[2] = {p->eW, p->eW + (size_t)n1 * n1};
+    CUCHK(p, arrow_update(q, (int)ld, d, z, al, mu, W, p->earw, st));
+    gemm(n1, n1, n1, 1.0, MatView{p->eQa, 1, ld}, MatView{W[0], 1, n1}, 0.0, p->eQa2, 1, ld, p->ws, p->ws_elems,
          st);
-    gemm(n1, n1, n1, 1.0, MatView{p->eQb, 1, ld}, MatView{p->eW + (size_t)n1 * n1, 1, n1}, 0.0, p->eQb2, 1, ld,
-         p->ws, p->ws_elems, st);
+    gemm(n1, n1, n1, 1.0, MatView{p->eQb, 1, ld}, MatView{W[1], 1, n1}, 0.0, p->eQb2, 1, ld, p->ws, p->ws_elems,
+         st);
     std::swap(p->eQa, p->eQa2);
     std::swap(p->eQb, p->eQb2);
-    p->hla = mua;
-    p->hlb = mub;
     ++p->eq;
   }
-  std::copy(p->hla.begin(), p->hla.end(), hl);
-  std::copy(p->hlb.begin(), p->hlb.end(), hl + ld);
-  CUCHK(p, cudaMemcpyAsync(p->ela, hl, sizeof(double) * j, cudaMemcpyHostToDevice, st));
-  CUCHK(p, cudaMemcpyAsync(p->elb, hl + ld, sizeof(double) * j, cudaMemcpyHostToDevice, st));
-  p->h2d_bytes += (int64_t)sizeof(double) * 2 * j;
-  TRY(sync(p));  // the staging buffer is reused by the next call
-  p->gal_basis_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  prof_end(p, CR_PHASE_BASIS);
   return CR_OK;
 }
 
@@ -1293,8 +1274,6 @@ void eig_reset(cr_problem* p) {
   if (!p->eQa) return;
   const int64_t ld = p->rcap;
   for (double* b : {p->eQa, p->eQa2, p->eQb, p->eQb2}) fill(ld * ld, 0.0, b, p->st);
-  p->hla.clear();
-  p->hlb.clear();
   p->eq = 0;
 }
 
@@ -1858,7 +1837,6 @@ void cr_destroy(cr_problem* p) {
       cudaFree(a.first);
   }
   if (p->hs) cudaFreeHost(p->hs);
-  if (p->eh) cudaFreeHost(p->eh);
   prof_resolve(p);
   for (auto e : p->ev_pool) cudaEventDestroy(e);
   for (auto e : p->open_ev)
@@ -2083,12 +2061,7 @@ cr_status cr_create(const cr_problem_desc* d_in, const cr_options* o, cr_problem
     if (m <= 128) CK(dalloc(p, &p->eCi, (size_t)rc * m * m));
     CK(dalloc(p, &p->eW, 2 * r2));
     CK(dalloc(p, &p->ebord, 2 * ((size_t)rc + 1)));
-    if (cudaMallocHost(&p->eh, sizeof(double) * (2 * ((size_t)rc + 1) + 2 * r2 + 2 * (size_t)rc)) != cudaSuccess) {
-      cudaGetLastError();
-      p->eh = nullptr;
-      p->err = "cudaMallocHost failed";
-      return abort_create(CR_ENOMEM);
-    }
+    CK(dalloc(p, &p->earw, 2 * arrow_work_doubles(rc)));
     if (opt.precision == CR_MIXED) {
       for (float** b : {&p->fQa, &p->fZz}) CK(dalloc(p, b, r2));
       for (float** b : {&p->fla, &p->flb}) CK(dalloc(p, b, rc));
@@ -2308,7 +2281,6 @@ cr_status cr_get_stats(cr_problem* p, cr_stats* s, int32_t reset) {
   }
   s->galerkin_eigen[0] = p->gal_eig_proj;
   s->galerkin_eigen[1] = p->gal_eig_finish;
-  s->galerkin_basis_ms = p->gal_basis_ms;
   for (int i = 0; i < CR_NPHASE; ++i) {
     s->phase_ms[i] = p->phase_ms[i];
     s->phase_calls[i] = p->phase_calls[i];
@@ -2319,7 +2291,6 @@ cr_status cr_get_stats(cr_problem* p, cr_stats* s, int32_t reset) {
     p->h2d_bytes = p->d2h_bytes = 0;
     p->learned_solves = p->fcg_fallbacks = p->mixed_handovers = 0;
     p->gal_eig_proj = p->gal_eig_finish = 0;
-    p->gal_basis_ms = 0.0;
     for (int i = 0; i < CR_NPHASE; ++i) {
       p->phase_ms[i] = 0.0;
       p->phase_calls[i] = 0;

@@ -280,6 +280,14 @@ struct GalEig {
   double *S = nullptr, *Yd = nullptr;
   T* Zz = nullptr;
 };
+// Arrowhead eigen-update of both eigenbases (cr_arrow.cu): for side s, the
+// eigen-decomposition of [diag(d) z; z^T alpha] (d: n ascending, alpha a device
+// scalar) into mu (n + 1, ascending; may alias d) and W ((n + 1)^2, ld n + 1).
+// work: 2 * arrow_work_doubles(nmax) doubles.
+size_t arrow_work_doubles(int nmax);
+cudaError_t arrow_update(int n, int nmax, const double* const d[2], const double* const z[2],
+                         const double* const alpha[2], double* const mu[2], double* const W[2], double* work,
+                         cudaStream_t st);
 // Diagonal of the eigenbasis Galerkin operator with each G_a replaced by its mean
 // diagonal g_a = tr(G_a) / j (g: m doubles, written):
 //   Dl(i, k) = lam (A2t_ii + 2 la_i lb_k + B2t_kk),  Den = Dl + sum_a g_a Ht(k, a)^2,

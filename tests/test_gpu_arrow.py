@@ -1,58 +1,35 @@
-"""The arrowhead eigen-decomposition (csrc/cr_host_arrow.h) that keeps the
-eigenbases of U^T L_y U and V^T L_x V up to date as the Galerkin projection
-(Eq. Proj_Sylv) grows by one border per greedy step.  Built on the CPU with
-g++ and checked against numpy's symmetric eigensolver and its defining
-identities: eigenvalues and M W = W diag(mu) to 5e-11 of the matrix's scale (the
+"""The device arrowhead eigen-decomposition (csrc/cr_arrow.cu, through
+cr_arrow_check) that keeps the eigenbases of U^T L_y U and V^T L_x V up to date
+as the Galerkin projection (Eq. Proj_Sylv) grows by one border per greedy step.
+Checked against numpy's symmetric eigensolver and the defining identities:
+eigenvalues and M W = W diag(mu) to 5e-11 of the matrix's scale (the
 eigenvectors are exact for a coupling vector recomputed from the computed
 roots, which differs from the given one by rounding), W^T W = I to 1e-13,
-including the deflated
-cases (zero couplings, repeated poles, an empty or a zero matrix) and the
-bordering identity it serves."""
-import ctypes as C
-import os
-import shutil
-import subprocess
-
+including the deflated cases (zero couplings, repeated poles, an empty or a
+zero matrix) and the bordering identity it serves."""
 import numpy as np
 import pytest
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER_DIR = os.path.join(ROOT, "paper_1808_05510_gb300", "csrc")
-
-WRAPPER = r"""
-#include "cr_host_arrow.h"
-extern "C" void t_arrow(int n, const double* d, const double* z, double alpha, double* mu, double* W) {
-  std::vector<double> dv(d, d + n), zv(z, z + n), m, w;
-  cr_host::arrow_eig(n, dv, zv, alpha, m, w);
-  std::copy(m.begin(), m.end(), mu);
-  std::copy(w.begin(), w.end(), W);
-}
-"""
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
-def lib(tmp_path_factory):
-    if shutil.which("g++") is None:
-        pytest.skip("g++ not available")
-    d = tmp_path_factory.mktemp("arrow")
-    src = d / "w.cpp"
-    src.write_text(WRAPPER)
-    so = d / "libw.so"
-    subprocess.run(["g++", "-std=c++17", "-O2", "-pthread", "-shared", "-fPIC", "-I", HEADER_DIR, str(src), "-o",
-                    str(so)], check=True)
-    L = C.CDLL(str(so))
-    dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="F_CONTIGUOUS")
-    L.t_arrow.argtypes = [C.c_int, dp, dp, C.c_double, dp, dp]
-    return L
+def lib():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1808_05510_gb300 import build
+
+    build.build()
+    from paper_1808_05510_gb300 import conreg
+
+    conreg.load()
+    return conreg
 
 
 def arrow(lib, d, z, alpha):
-    n = len(d)
-    mu = np.zeros(n + 1)
-    W = np.zeros((n + 1, n + 1), order="F")
-    lib.t_arrow(n, np.asfortranarray(d, dtype=np.float64), np.asfortranarray(z, dtype=np.float64), float(alpha), mu,
-                W)
-    return mu, W
+    return lib.arrow_check(np.asarray(d, dtype=np.float64), np.asarray(z, dtype=np.float64), float(alpha))
 
 
 def dense(d, z, alpha):
