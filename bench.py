@@ -9,7 +9,8 @@ box, 7-point Laplacians, 28 Gaussian injections, lambda = 100, rank <= 100).
 
 Reported: rank-1 updates per second (whole job, all GPUs), the time to the
 relative residual target when reached, an end-to-end number through the public
-API with host buffers, the roofline of the dominant kernel (the cluster PCG),
+API with host buffers, the roofline of the dominant kernel (the PCG kernel of
+the side with the larger share of the step),
 the CPU float64 oracle as a baseline, SM clocks during the timed region, and
 the number of library kernel launches.
 
@@ -149,31 +150,28 @@ def peaks():
         return 6800.0, "of fallback"
 
 
-def pcg_traffic(form: str):
-    """DRAM bytes per PCG launch from the committed ncu summary, or None when the
-    kernel source has changed since the counters were taken."""
+KERNEL_SOURCES = {"pcg_reg_kernel": "cr_pcg.cu", "pcg_mg_kernel": "cr_mg.cu", "pcg_grid_kernel": "cr_pcg_grid.cu"}
+
+
+def pcg_traffic(kernel: str, form: str, side: int):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (profiles/<kernel>_traffic.json), or None when there is none or the kernel's
+    source has changed since the counters were taken."""
     import hashlib
 
     try:
-        with open(os.path.join(ROOT, "profiles", "pcg_reg_kernel_traffic.json")) as f:
+        with open(os.path.join(ROOT, "profiles", kernel + "_traffic.json")) as f:
             d = json.load(f)
-        with open(os.path.join(ROOT, "paper_1808_05510_gb300", "csrc", "cr_pcg.cu"), "rb") as f:
+        src = KERNEL_SOURCES[kernel]
+        with open(os.path.join(ROOT, "paper_1808_05510_gb300", "csrc", src), "rb") as f:
             h = hashlib.sha256(f.read()).hexdigest()[:16]
         if h != d["source_sha256_16"]:
             return None
         b = d["dram_bytes_per_launch"]
-        pre = "fp64" if form == "fp64" else "f32"
-        return 0.5 * (b[pre + "_u"] + b[pre + "_v"])
+        key = ("fp64" if form == "fp64" else "f32") + ("_u" if side == 0 else "_v")
+        return b.get(key)
     except Exception:
         return None
-
-
-def pcg_bytes_per_iter(n: int, slots: int = 6, word: float = 8.0) -> float:
-    """Algorithmic bytes of one Chronopoulos-Gear PCG iteration: read and write
-    r, x, p, s (8 words), read the Jacobi diagonal and the data diagonal (2
-    words), read the neighbour table once (4 B per slot); word = 8 (float64) or
-    4 (float32)."""
-    return n * (10.0 * word + 4.0 * slots)
 
 
 # ----------------------------------------------------------------------------- CPU oracle
@@ -296,17 +294,28 @@ def run_ours(args, rank, world, local_rank):
         value = all_ranks / (t_max / 1e3)
         reached = [i for i in infos if i["stop_name"] == "relres"]
         ttr = (sum(m for m, i in zip(ms, infos) if i["stop_name"] == "relres") / len(reached) / 1e3) if reached else None
-        # the PCG kernel's own launches (CUDA events around each launch, on the
+        # each side's PCG kernel launches (CUDA events around each launch, on the
         # problem's stream); the mixed form's sub-solves are several float32
-        # launches inside float64 refinement
+        # launches inside float64 refinement.  Algorithmic bytes per iteration come
+        # from the library (the multigrid hierarchy's sizes, or the Jacobi count).
         pcg_ms = stats["phase_ms"]["pcg_u"] + stats["phase_ms"]["pcg_v"]
-        kern_ms = stats["phase_ms"]["pcg_kernel"]
-        kern_calls = max(1, stats["phase_calls"]["pcg_kernel"])
-        iters_per_launch = stats["pcg_iters"] / kern_calls
-        word = 8.0 if prec == CR_FP64 else 4.0
-        bytes_per_launch = iters_per_launch * pcg_bytes_per_iter(int(0.5 * (p.nx + p.ny)), word=word)
-        avg_launch_s = kern_ms / kern_calls / 1e3
-        achieved = bytes_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
+        kern_ms = stats["phase_ms"]["pcg_kernel"] + stats["phase_ms"]["pcg_kernel_v"]
+        sides = []
+        for side, ph in ((0, "pcg_kernel"), (1, "pcg_kernel_v")):
+            kms = stats["phase_ms"][ph]
+            calls = max(1, stats["phase_calls"][ph])
+            its = stats["pcg_iters_side"][side]
+            ipl = its / calls
+            avg_s = kms / calls / 1e3
+            bpi = stats["pcg_bytes_per_iter"][side]
+            kname = ("pcg_mg_kernel" if stats["pcg_multigrid"][side] else
+                     "pcg_reg_kernel" if stats["pcg_cluster"][side] else "pcg_grid_kernel")
+            sides.append({"side": "uv"[side], "kernel": kname, "kernel_ms_per_step": kms / steps, "launches": calls,
+                          "iters": its, "iters_per_launch": ipl, "avg_launch_us": avg_s * 1e6,
+                          "us_per_iter": avg_s * 1e6 / max(ipl, 1e-9), "bytes_per_iter": bpi,
+                          "achieved": ipl * bpi / avg_s / 1e9 if avg_s > 0 else 0.0,
+                          "share_of_step": kms / tot_ms if tot_ms > 0 else None})
+        dom = max(sides, key=lambda d: d["kernel_ms_per_step"])
         return {"value": value, "ms_per_step": t_max / steps, "steps": steps, "warmup": warmup,
                 "precond": {CR_PRECOND_JACOBI: "jacobi", CR_PRECOND_LEARNED: "learned (flexible CG, Jacobi judge)",
                             CR_PRECOND_MULTIGRID: "multigrid", CR_PRECOND_AUTO: "auto (multigrid on the v side; "
@@ -318,8 +327,8 @@ def run_ours(args, rank, world, local_rank):
                 "galerkin_cg_iters_per_step": sum(i["cg_iters"] for i in infos) / steps,
                 "phase_ms_per_step": {k: v / steps for k, v in stats["phase_ms"].items() if v},
                 "gpu_launches": stats["launches"], "clocks": clk.summary(),
-                "pcg": {"achieved": achieved, "avg_launch_us": avg_launch_s * 1e6, "iters_per_launch": iters_per_launch,
-                        "us_per_iter": avg_launch_s * 1e6 / max(iters_per_launch, 1e-9),
+                "galerkin_eigen_projections": stats["galerkin_eigen"],
+                "pcg": {"dominant": dom, "sides": sides,
                         "share_of_step": pcg_ms / tot_ms if tot_ms > 0 else None,
                         "kernel_share_of_step": kern_ms / tot_ms if tot_ms > 0 else None},
                 **({"judge": {"learned_solves": stats["learned_solves"], "fallbacks": stats["learned_fallbacks"],
@@ -358,13 +367,15 @@ def run_ours(args, rank, world, local_rank):
     post = None if args.no_post else measure_post(p, args, CR_MIXED if args.precision == "mixed" else CR_FP64)
     head = forms[args.precision]
     hbm, peak_kind = peaks()
-    roofline = {"bound": "hbm", "achieved": head["pcg"]["achieved"], "peak": hbm, "unit": "GB/s",
-                "frac": head["pcg"]["achieved"] / hbm, "traffic": pcg_traffic(args.precision),
-                "kernel": "pcg_reg_kernel (cluster PCG)",
-                "peak_kind": peak_kind, "pcg_share_of_step": head["pcg"]["share_of_step"],
-                "kernel_share_of_step": head["pcg"]["kernel_share_of_step"],
-                "avg_launch_us": head["pcg"]["avg_launch_us"], "iters_per_launch": head["pcg"]["iters_per_launch"],
-                "us_per_iter": head["pcg"]["us_per_iter"]}
+    dom = head["pcg"]["dominant"]
+    roofline = {"bound": "hbm", "achieved": dom["achieved"], "peak": hbm, "unit": "GB/s",
+                "frac": dom["achieved"] / hbm,
+                "traffic": pcg_traffic(dom["kernel"], args.precision, "uv".index(dom["side"])),
+                "kernel": f"{dom['kernel']} ({dom['side']} side, the largest kernel share of the step)",
+                "peak_kind": peak_kind, "bytes_per_iter": dom["bytes_per_iter"],
+                "kernel_share_of_step": dom["share_of_step"], "pcg_share_of_step": head["pcg"]["share_of_step"],
+                "avg_launch_us": dom["avg_launch_us"], "iters_per_launch": dom["iters_per_launch"],
+                "us_per_iter": dom["us_per_iter"]}
     out = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",

@@ -202,9 +202,10 @@ typedef enum {
   CR_PHASE_ORTH = 3,     /* orthogonalisation and projected coefficient matrices */
   CR_PHASE_GALERKIN = 4, /* Galerkin CG on Eq. (Proj_Sylv) and the masked data residual */
   CR_PHASE_RESID = 5,    /* residual norm, objective, dW */
-  CR_PHASE_PCG_KERNEL = 6, /* the Jacobi-PCG kernel launches alone (inside PCG_U / PCG_V) */
+  CR_PHASE_PCG_KERNEL = 6, /* the u side's PCG kernel launches alone (inside PCG_U) */
   CR_PHASE_BASIS = 7,    /* eigenbasis updates of the Galerkin CG's eigenbasis form (inside GALERKIN) */
-  CR_NPHASE = 8
+  CR_PHASE_PCG_KERNEL_V = 8, /* the v side's PCG kernel launches alone (inside PCG_V) */
+  CR_NPHASE = 10
 } cr_phase;
 
 typedef struct {
@@ -223,6 +224,10 @@ typedef struct {
   int64_t pcg_multigrid[2];       /* levels of the multigrid preconditioner per side (0 = not in use) */
   int64_t galerkin_eigen[2];      /* projections solved in the eigenbasis form (0), of which the
                                      original-basis CG had to finish (1) */
+  int64_t pcg_iters_side[2];      /* PCG iterations of the u side (0) and the v side (1) */
+  double pcg_bytes_per_iter[2];   /* algorithmic bytes of one iteration of each side's PCG kernel in the
+                                     form's working precision, counted as if every vector and matrix entry
+                                     it touches were streamed from memory (the kernels keep them on chip) */
 } cr_stats;
 
 /* Fill *o with defaults (struct_size set).  Always succeeds for o != NULL. */

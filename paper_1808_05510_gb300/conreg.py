@@ -73,15 +73,16 @@ class cr_proj_info(C.Structure):
     _fields_ = [("iters", C.c_int32), ("relres", C.c_double)]
 
 
-PHASES = ["pcg_u", "pcg_v", "rhs", "orth", "galerkin", "resid", "pcg_kernel", "basis"]
+PHASES = ["pcg_u", "pcg_v", "rhs", "orth", "galerkin", "resid", "pcg_kernel", "basis", "pcg_kernel_v", "p9"]
 
 
 class cr_stats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("pcg_solves", C.c_int64), ("pcg_iters", C.c_int64),
-                ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("phase_ms", C.c_double * 8), ("phase_calls", C.c_int64 * 8),
+                ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("phase_ms", C.c_double * 10), ("phase_calls", C.c_int64 * 10),
                 ("learned_solves", C.c_int64), ("learned_fallbacks", C.c_int64), ("learned_off", C.c_int64),
                 ("mixed_handovers", C.c_int64), ("pcg_cluster", C.c_int64 * 2),
-                ("pcg_multigrid", C.c_int64 * 2), ("galerkin_eigen", C.c_int64 * 2)]
+                ("pcg_multigrid", C.c_int64 * 2), ("galerkin_eigen", C.c_int64 * 2),
+                ("pcg_iters_side", C.c_int64 * 2), ("pcg_bytes_per_iter", C.c_double * 2)]
 
 
 class cr_solve_info(C.Structure):
@@ -491,13 +492,15 @@ class ConReg:
         _check(self._lib.cr_get_stats(self.h, C.byref(s), int(reset)), self.h, "cr_get_stats")
         return {"launches": s.launches, "pcg_solves": s.pcg_solves, "pcg_iters": s.pcg_iters,
                 "h2d_bytes": s.h2d_bytes, "d2h_bytes": s.d2h_bytes,
-                "phase_ms": {PHASES[i]: s.phase_ms[i] for i in range(8)},
-                "phase_calls": {PHASES[i]: s.phase_calls[i] for i in range(8)},
+                "phase_ms": {PHASES[i]: s.phase_ms[i] for i in range(len(PHASES))},
+                "phase_calls": {PHASES[i]: s.phase_calls[i] for i in range(len(PHASES))},
                 "learned_solves": s.learned_solves, "learned_fallbacks": s.learned_fallbacks,
                 "learned_off": s.learned_off, "mixed_handovers": s.mixed_handovers,
                 "pcg_cluster": [s.pcg_cluster[0], s.pcg_cluster[1]],
                 "pcg_multigrid": [s.pcg_multigrid[0], s.pcg_multigrid[1]],
-                "galerkin_eigen": [s.galerkin_eigen[0], s.galerkin_eigen[1]]}
+                "galerkin_eigen": [s.galerkin_eigen[0], s.galerkin_eigen[1]],
+                "pcg_iters_side": [s.pcg_iters_side[0], s.pcg_iters_side[1]],
+                "pcg_bytes_per_iter": [s.pcg_bytes_per_iter[0], s.pcg_bytes_per_iter[1]]}
 
     def cr_solve_u(self, v, rhs, allow_notconv: bool = False):
         """(solution, iterations); with ``allow_notconv`` a solve that stopped at

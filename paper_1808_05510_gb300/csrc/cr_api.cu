@@ -272,7 +272,7 @@ struct cr_problem {
   cudaEvent_t open_ev[CR_NPHASE] = {};
   double phase_ms[CR_NPHASE] = {};
   int64_t phase_calls[CR_NPHASE] = {};
-  int64_t pcg_solves = 0, pcg_iters = 0;
+  int64_t pcg_solves = 0, pcg_iters = 0, pcg_iters_side[2] = {0, 0};
   int64_t h2d_bytes = 0, d2h_bytes = 0;
   long long launch_base = 0;
 };
@@ -582,9 +582,25 @@ cr_status build_mg(cr_problem* p, const cr_csr& c, const DevLap& L, DevMg& g) {
   const cr_mg::Hierarchy H = cr_mg::build(A, kMgCoarseMax, kMgMaxLev);
   const int nlev = (int)H.lev.size();
   if (nlev < 2 || H.lev.back().L.rows > kMgCoarseMax) return CR_OK;
+  double bytes_iter[2];
+  for (int wi = 0; wi < 2; ++wi) {
+    const double w = wi == 0 ? 4.0 : 8.0;
+    double vc = 0.0;
+    for (int l = 0; l + 1 < nlev; ++l) {
+      const cr_mg::Level& HL = H.lev[l];
+      const double nl = HL.L.rows;
+      vc += 4.0 * ((double)HL.L.nnz() * (4.0 + w) + 3.0 * nl * w) +
+            (double)(HL.P.nnz() + HL.R.nnz()) * (4.0 + w) + 2.0 * nl * w;
+    }
+    const double ncd = H.lev.back().L.rows;
+    vc += 2.0 * ncd * ncd * 8.0;
+    bytes_iter[wi] = (double)n * (10.0 * w + 4.0 * L.K) + 2.0 * vc;
+  }
   std::vector<double> Q, mu;
   if (!cr_mg::pencil_basis(H.lev.back().L, H.lev.back().M, Q, mu)) return CR_OK;
   DevMg h{};
+  h.bytes_iter[0] = bytes_iter[0];
+  h.bytes_iter[1] = bytes_iter[1];
   h.nlev = nlev;
   h.nc = H.lev.back().L.rows;
   h.ld = nlev - 1;
@@ -984,16 +1000,17 @@ bool use_mg(const cr_problem* p, int side, bool fp32) {
 }
 
 cr_status run_pcg(cr_problem* p, int side, const double* b, double* x, int maxit, double tol, bool fp32) {
+  const int kph = side == 0 ? CR_PHASE_PCG_KERNEL : CR_PHASE_PCG_KERNEL_V;
   if (use_mg(p, side, fp32)) {
-    prof_begin(p, CR_PHASE_PCG_KERNEL);
+    prof_begin(p, kph);
     CUCHK(p, mg_pcg_launch(pcg_args(p, side, b, x, maxit, tol, fp32), p->mg[side], side, p->st));
-    prof_end(p, CR_PHASE_PCG_KERNEL);
+    prof_end(p, kph);
     return CR_OK;
   }
   if (!use_grid_pcg(p, side, fp32)) {
-    prof_begin(p, CR_PHASE_PCG_KERNEL);
+    prof_begin(p, kph);
     CUCHK(p, pcg_launch(pcg_args(p, side, b, x, maxit, tol, fp32), side, p->st));
-    prof_end(p, CR_PHASE_PCG_KERNEL);
+    prof_end(p, kph);
     return CR_OK;
   }
   const int nmax = std::max(p->nx, p->ny);
@@ -1015,10 +1032,10 @@ cr_status run_pcg(cr_problem* p, int side, const double* b, double* x, int maxit
   const double* coef = p->coef + (side == 0 ? 0 : 2);
   fcg_jacobi_diag(L, p->lam, coef, side, p->m, p->Om, p->ny, p->xi, p->xl, p->svec, p->pomt, p->pdinv, p->st);
   PcgArgs a = pcg_args(p, side, b, x, maxit, tol, fp32);
-  prof_begin(p, CR_PHASE_PCG_KERNEL);
+  prof_begin(p, kph);
   CUCHK(p, pcg_grid_launch(a, side, p->xc_ptr, p->xc_row, p->xc_val, p->pg_work, p->pg_part, p->pg_ypart,
                            p->pg_yglob, p->pg_bar, p->pg_err, std::min(nb, std::max(1, L.n / 64)), p->st));
-  prof_end(p, CR_PHASE_PCG_KERNEL);
+  prof_end(p, kph);
   TRY(readback(p, 0, 1, true));
   if (p->hs->stat[side].status == 3) return fail(p, CR_ETIMEOUT, "grid-wide PCG barrier timed out");
   return CR_OK;
@@ -1718,6 +1735,8 @@ cr_status do_rank_one(cr_problem* p, cr_rank1_info* info) {
     const PcgStat* s = p->hs->stat;
     p->pcg_solves += 2;
     p->pcg_iters += s[0].iters + s[1].iters;
+    p->pcg_iters_side[0] += s[0].iters;
+    p->pcg_iters_side[1] += s[1].iters;
     itu += s[0].iters;
     itv += s[1].iters;
     worst = std::max(worst, std::max(s[0].relres, s[1].relres));
@@ -2281,6 +2300,18 @@ cr_status cr_get_stats(cr_problem* p, cr_stats* s, int32_t reset) {
   }
   s->galerkin_eigen[0] = p->gal_eig_proj;
   s->galerkin_eigen[1] = p->gal_eig_finish;
+  for (int side = 0; side < 2; ++side) {
+    const bool f32 = p->opt.precision == CR_MIXED;
+    const double w = f32 ? 4.0 : 8.0;
+    const DevLap& L = side == 0 ? p->Ly : p->Lx;
+    s->pcg_iters_side[side] = p->pcg_iters_side[side];
+    double b = (double)L.n * (10.0 * w + 4.0 * L.K);  // Jacobi PCG (Chronopoulos-Gear)
+    if (use_mg(p, side, f32)) {
+      b = p->mg[side].bytes_iter[f32 ? 0 : 1];
+      if (side == 1 && p->mg[1].smw) b += (double)L.n * p->m * w;  // the Woodbury correction reads M0^-1 X
+    }
+    s->pcg_bytes_per_iter[side] = b;
+  }
   for (int i = 0; i < CR_NPHASE; ++i) {
     s->phase_ms[i] = p->phase_ms[i];
     s->phase_calls[i] = p->phase_calls[i];
@@ -2288,6 +2319,7 @@ cr_status cr_get_stats(cr_problem* p, cr_stats* s, int32_t reset) {
   if (reset) {
     p->launch_base = cr::g_launches.load();
     p->pcg_solves = p->pcg_iters = 0;
+    p->pcg_iters_side[0] = p->pcg_iters_side[1] = 0;
     p->h2d_bytes = p->d2h_bytes = 0;
     p->learned_solves = p->fcg_fallbacks = p->mixed_handovers = 0;
     p->gal_eig_proj = p->gal_eig_finish = 0;

@@ -165,6 +165,10 @@ struct DevMg {
   const double* cmu = nullptr; // nc
   const double* xn2 = nullptr; // v side: |X_a|^2 per injection (mean data weight of the shift)
   int lvl_elems = 0;           // shared-memory elements of the levels >= 1
+  // algorithmic bytes of one PCG iteration ([0] float32, [1] float64; host accounting):
+  // the fine-level PCG as the Jacobi count plus, for each of the two V-cycles, four
+  // sweeps, restriction and prolongation per level and the coarsest dense solve
+  double bytes_iter[2] = {0.0, 0.0};
   size_t smem[2] = {0, 0};     // dynamic shared memory of the kernel for T = float, double (0: does not fit)
   // Tables each CTA fills at launch for the rows it owns: the 32-bit
   // cluster-window address of every referenced entry (relative to its level's

@@ -1,10 +1,14 @@
 """Representative kernel cases for profiling runs (ncu) on the visual-cortex workload.
 
-    python -m paper_1808_05510_gb300.profile_cases pcg fp64|mixed
+    python -m paper_1808_05510_gb300.profile_cases pcg fp64|mixed [jacobi|auto]
         one u-side and one v-side ALS solve (Eqs. ALS_linsys, ALS_linsys_v) for the
-        first ALS vector v = R_0^T 1 / |R_0^T 1|, to relative residual 1e-8, twice
-    python -m paper_1808_05510_gb300.profile_cases galerkin fp64|mixed
-        two Galerkin projections (Eq. Proj_Sylv) at rank 60 from a float64 greedy run
+        first ALS vector v = R_0^T 1 / |R_0^T 1|, to relative residual 1e-8, twice;
+        jacobi (default): Jacobi PCG on both sides; auto: the automatic choice
+        (multigrid PCG on the v side, pcg_mg_kernel); prints iterations and the
+        CUDA-event time of each solve
+    python -m paper_1808_05510_gb300.profile_cases galerkin fp64|mixed [eigen|jacobi]
+        two Galerkin projections (Eq. Proj_Sylv) at rank 60 from a float64 greedy run,
+        in the eigenbasis form (default) or the original-basis Jacobi form
     python -m paper_1808_05510_gb300.profile_cases assembly tc
         three tensor-core assemblies of G_a = U^T diag(Omega_a) U at rank 100
     python -m paper_1808_05510_gb300.profile_cases post fp64
@@ -24,33 +28,47 @@ import sys
 import numpy as np
 
 
-def pcg(form: str) -> None:
+def pcg(form: str, precond: str = "jacobi") -> None:
+    import torch
+
     from . import synth
-    from .conreg import CR_FP64, CR_MIXED, ConReg
+    from .conreg import CR_FP64, CR_MIXED, CR_PRECOND_AUTO, CR_PRECOND_JACOBI, ConReg
 
     p = synth.visual_cortex()
     prec = CR_MIXED if form == "mixed" else CR_FP64
+    pc = CR_PRECOND_AUTO if precond == "auto" else CR_PRECOND_JACOBI
     with ConReg.from_problem(p, r_cap=4) as g0:
         v = g0.cr_apply_residual(np.ones(p.ny), trans=True)
         v /= np.linalg.norm(v)
         rhs_u = g0.cr_apply_residual(v)
         u = rhs_u / np.linalg.norm(rhs_u)
         rhs_v = g0.cr_apply_residual(u, trans=True)
-    with ConReg.from_problem(p, r_cap=4, precision=prec, pcg_tol=1e-8) as g:
+    with ConReg.from_problem(p, r_cap=4, precision=prec, pcg_tol=1e-8, precond=pc) as g:
+        stream = g.stream
         for _ in range(2):
-            print("iterations", g.cr_solve_u(v, rhs_u)[1], g.cr_solve_v(u, rhs_v)[1], flush=True)
+            out = []
+            for solve, a, b in ((g.cr_solve_u, v, rhs_u), (g.cr_solve_v, u, rhs_v)):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                _, it = solve(a, b)
+                e1.record(stream)
+                e1.synchronize()
+                out.append((it, round(e0.elapsed_time(e1), 3)))
+            print("iterations, ms (u, v):", out, "multigrid levels:", g.cr_get_stats()["pcg_multigrid"], flush=True)
 
 
-def galerkin(form: str) -> None:
+def galerkin(form: str, gform: str = "eigen") -> None:
     from . import synth
-    from .conreg import CR_FP64, CR_MIXED, ConReg
+    from .conreg import CR_FP64, CR_GALERKIN_EIGEN, CR_GALERKIN_JACOBI, CR_MIXED, ConReg
 
     p = synth.visual_cortex()
     with ConReg.from_problem(p, r_cap=100) as g:
         g.cr_solve(60, 1e-9, 0.0)
         U, Z, V = g.cr_get_factors()
     prec = CR_MIXED if form == "mixed" else CR_FP64
-    with ConReg.from_problem(p, r_cap=100, precision=prec) as g:
+    gf = CR_GALERKIN_JACOBI if gform == "jacobi" else CR_GALERKIN_EIGEN
+    with ConReg.from_problem(p, r_cap=100, precision=prec, galerkin_form=gf) as g:
         for k in range(2):
             g.cr_set_factors(U, Z * (1.0 + 1e-3 * (k + 1)), V)
             print(g.cr_project(5e-10), flush=True)
@@ -131,4 +149,5 @@ if __name__ == "__main__":
     if case == "pcg_stress":
         pcg_stress(form, int(sys.argv[3]) if len(sys.argv) > 3 else 2)
     else:
-        {"pcg": pcg, "galerkin": galerkin, "assembly": assembly, "post": post}[case](form)
+        extra = sys.argv[3:4]
+        {"pcg": pcg, "galerkin": galerkin, "assembly": assembly, "post": post}[case](form, *extra)
