@@ -358,7 +358,7 @@ def run_ours(args, rank, world, local_rank):
         forms["learned"] = lf
         net.close()
     if not args.no_batch:
-        forms["batched"] = measure_batch(args, rank, world, dev)
+        forms["batched"] = measure_batch(args, rank, world, dev, precond=head_pc)
     ttr_toy = None if args.no_ttr else measure_ttr_toy(args)
     ttr_visual = None if args.no_ttr else measure_ttr(p, args, head_pc, r_cap=args.ttr_r,
                                                       label="visual-cortex workload (7,530 voxels, 28 injections, "
@@ -394,7 +394,7 @@ def run_ours(args, rank, world, local_rank):
         for k in range(args.steps + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            with ConReg.from_problem(p, r_cap=args.r_max, precision=prec_e2e) as ge:
+            with ConReg.from_problem(p, r_cap=args.r_max, precision=prec_e2e, precond=head_pc) as ge:
                 info = ge.cr_solve(args.r_max, args.tau, args.relres)
                 U, Z, V = ge.cr_get_factors()
                 st = ge.cr_get_stats()
@@ -590,7 +590,7 @@ def measure_ttr_toy(args, runs: int = 3):
     return out
 
 
-def measure_batch(args, rank=0, world=1, dev="cuda"):
+def measure_batch(args, rank=0, world=1, dev="cuda", precond=None):
     """Batched form: the lambda x fold sweep (16 lambdas log-spaced 1..1e6 x 5 folds
     of a 126-injection, ~15,000-voxel data set; every member fits 96-106
     injections) in the mixed form, after the autotuner picked its launch shape.
@@ -608,17 +608,18 @@ def measure_batch(args, rank=0, world=1, dev="cuda"):
     mem_all = _synth.sweep_members(bp.m, _synth.lambda_grid(), folds)
     mem = replicas.shard_members(mem_all, rank, world)
     gen_s = time.perf_counter() - t0
-    solve_batch(bp, mem[:9], r_max=2, tau=args.tau, precision=CR_MIXED)  # warm-up
-    shape = sweep.autotune(bp, mem, r_probe=2, tau=args.tau, precision=CR_MIXED)
+    pc = {} if precond is None else {"precond": precond}
+    solve_batch(bp, mem[:9], r_max=2, tau=args.tau, precision=CR_MIXED, **pc)  # warm-up
+    shape = sweep.autotune(bp, mem, r_probe=2, tau=args.tau, precision=CR_MIXED, **pc)
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
         res, sec = sweep._timed_batch(bp, mem, args.batch_r, tau=args.tau, relres_target=args.relres,
                                       concurrency=shape["concurrency"], cluster_size=shape["cluster_size"],
-                                      precision=CR_MIXED)
+                                      precision=CR_MIXED, **pc)
     ranks, ms_max = replicas.aggregate(sum(r["rank"] for r in res), 1e3 * sec, world, dev)
     sec = ms_max / 1e3
     sample = mem[::max(1, 10 // world)]  # 8 members, every other lambda (fold 0)
     seq, seq_sec = sweep._timed_batch(bp, sample, args.batch_r, tau=args.tau, relres_target=args.relres,
-                                      concurrency=1, precision=CR_MIXED)
+                                      concurrency=1, precision=CR_MIXED, **pc)
     seq_ranks, seq_ms = replicas.aggregate(sum(r["rank"] for r in seq), 1e3 * seq_sec, world, dev)
     seq_sec = seq_ms / 1e3
     # per-member scores of every rank, for the cross-validation curve

@@ -57,9 +57,10 @@ typedef enum { CR_FP64 = 0, CR_MIXED = 1 } cr_precision;
  * weight over lam), hierarchy built once from L at cr_create; on the v side
  * with at most 32 injections the data term is added exactly by
  * Sherman-Morrison-Woodbury; sizes whose vectors do not fit one thread-block
- * cluster fall back to Jacobi.  CR_PRECOND_AUTO: multigrid on the v side; on
- * the u side multigrid in the float64 form or above 20,000 rows, Jacobi
- * otherwise (there Jacobi's few cheap float32 iterations are faster). */
+ * cluster fall back to Jacobi.  CR_PRECOND_AUTO: multigrid in the float64
+ * form; in the mixed form multigrid above 20,000 rows or for lambda >= 1e3
+ * (where the Laplacian term dominates and Jacobi's iteration count grows),
+ * Jacobi otherwise (there its many cheap float32 iterations are faster). */
 typedef enum {
   CR_PRECOND_JACOBI = 0,
   CR_PRECOND_LEARNED = 1,

@@ -985,18 +985,24 @@ bool use_grid_pcg(const cr_problem* p, int side, bool fp32) {
 // One Jacobi-PCG solve on the cluster-resident kernel, or on the grid-wide
 // kernel (use_grid_pcg; that path waits for the result, to turn a grid
 // barrier timeout into CR_ETIMEOUT).
-// Rows above which the automatic choice takes multigrid on the u side in float32 too.
+// The automatic choice in float32: multigrid above this many rows, or from this
+// lambda on (measured on GB300 in the mixed form: at lambda = 100 on 7,530 voxels
+// Jacobi reaches relres 1e-6 in 11.5 s against multigrid's 15.0 s on the v side;
+// in the lambda sweep over 1 .. 1e6 on 15,000 voxels multigrid is faster overall
+// and leaves fewer members at the iteration cap).
 constexpr int kMgAutoRows = 20000;
+constexpr double kMgAutoLambda = 1e3;
 
 bool use_mg(const cr_problem* p, int side, bool fp32) {
   const DevMg& g = p->mg[side];
   if (!(g.nlev >= 2 && g.smem[fp32 ? 0 : 1] > 0)) return false;
   if (p->opt.precond == CR_PRECOND_MULTIGRID) return true;
   if (p->opt.precond != CR_PRECOND_AUTO) return false;
-  // measured on GB300 (7,530 voxels): a multigrid iteration costs ~80 us (float32) / ~95 us (float64)
-  // against ~5 / ~12 us for Jacobi, while it cuts the u side's iterations ~10x and the v side's ~50x
+  // measured on GB300 (7,530 voxels): a multigrid iteration costs ~80-125 us (float32) / ~90-165 us
+  // (float64) against ~4-6 / ~9-13 us for Jacobi, while it cuts the iterations 10-50x; in float64
+  // that always pays, in float32 only where Jacobi's iteration count is large
   const DevLap& L = side == 0 ? p->Ly : p->Lx;
-  return side == 1 || !fp32 || L.n > kMgAutoRows;
+  return !fp32 || L.n > kMgAutoRows || p->lam >= kMgAutoLambda;
 }
 
 cr_status run_pcg(cr_problem* p, int side, const double* b, double* x, int maxit, double tol, bool fp32) {
