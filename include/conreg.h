@@ -338,8 +338,7 @@ cr_status cr_get_stats(struct cr_problem* p, cr_stats* s, int32_t reset);
  * until the process exits, so n may be at most 131072 (larger n: CR_EINVAL).
  * Every call looks up that array's device address in the current context
  * (with the device current); the first call on a device also loads the
- * library's device code there, so make it before any stream capture.  All
- * calls share the array: calls whose kernels overlap on the GPU (other streams
+ * library's device code there.  All calls share the array: calls whose kernels overlap on the GPU (other streams
  * or host threads) race and return garbage.  The call waits for `stream` to
  * finish before it returns (it reads its status words back).  Errors are
  * described by cr_last_error(NULL). */

@@ -17,7 +17,7 @@
 // the kernel's launch attributes; both are cheap host calls and always refer
 // to the current context, so a cudaDeviceReset between calls leaves nothing
 // stale.  The first call on a device also loads the library's device code
-// there; make that first call before any stream capture.  All calls share the
+// there.  All calls share the
 // one array and it keeps the last call's contents: the status words are
 // cleared before each launch, and two calls whose kernels overlap on the GPU
 // (different streams, or several host threads) race on the array and produce
