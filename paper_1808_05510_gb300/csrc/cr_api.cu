@@ -15,7 +15,9 @@
 // vector (zcoef).
 //
 // Residual norm (Algorithm 1's residual; relative Frobenius norm).  R is never
-// formed: R = [E | UU] M [X | VV]^T with a block core M (build_core).  With
+// formed: R = [E | UU] M [X | VV]^T with a block core M (the identity on the m
+// data columns; for the panel block (3p+s, 3q+t): -lam Z(p,q) for (s,t) = (0,2)
+// and (2,0), -2 lam Z(p,q) for (1,1); do_relres applies it without forming it).  With
 // orthonormal bases Q_P of span[E | UU] and Q_Q of span[X | VV] and C_P = Q_P^T
 // [E | UU], C_Q = Q_Q^T [X | VV], ||R||_F = ||C_P M C_Q^T||_F.  The bases of
 // UU, X and VV grow by Gram-Schmidt as columns are appended; only E (m columns)
@@ -254,7 +256,7 @@ struct cr_problem {
         *fG = nullptr, *fF = nullptr, *fZ = nullptr, *fR = nullptr, *fPa = nullptr, *fPb = nullptr, *fQ = nullptr,
         *fT2 = nullptr, *fT1 = nullptr, *fTH = nullptr, *fGw = nullptr, *fzb = nullptr;
   double *QL = nullptr, *CL = nullptr, *QR = nullptr, *CRm = nullptr, *Cx = nullptr, *Cx2 = nullptr, *Ep = nullptr,
-         *CE = nullptr, *CP = nullptr, *Mc = nullptr, *T1 = nullptr, *T2 = nullptr, *gram = nullptr, *tmat = nullptr;
+         *CE = nullptr, *CP = nullptr, *T1 = nullptr, *T2 = nullptr, *gram = nullptr, *tmat = nullptr;
   int nQL = 0, nQR = 0, nQX = 0;
   int64_t ldcl = 0, ldcr = 0, ldcx = 0, ldcp = 0, ldm = 0;
   double* ws = nullptr;
@@ -1672,9 +1674,15 @@ cr_status do_relres(cr_problem* p, double* relres) {
     copy2d(k, 3 * j, p->CL, p->ldcl, p->CP + (size_t)m * ldcp, ldcp, st);
   }
   if (ke > 0) copy2d(ke, m, p->CE, m, p->CP + k, ldcp, st);
-  build_core(m, j, p->Z, p->rcap, p->lam, p->Mc, p->ldm, st);
-  gemm(kr, nc, nc, 1.0, MatView{p->CP, 1, ldcp}, MatView{p->Mc, 1, p->ldm}, 0.0, p->T1, 1, ldcp, p->ws, p->ws_elems,
-       st);
+  // T1 = C_P M_c.  The core M_c is the identity on the m data columns and
+  // -lam (Z kron J) on the panels (column 3p + s of a panel block is L^s u_p; J the
+  // anti-diagonal (1, 2, 1)), so T1 is the data columns of C_P and, for t = 0, 1, 2,
+  // the panel columns t of T1 = -lam c_t (panel columns 2 - t of C_P) Z, c_1 = 2:
+  // three products of kr x j x j instead of one of kr x (m + 3j)^2.
+  copy2d(kr, m, p->CP, ldcp, p->T1, ldcp, st);
+  for (int t = 0; t < 3; ++t)
+    gemm(kr, j, j, -p->lam * (t == 1 ? 2.0 : 1.0), MatView{p->CP + (size_t)(m + 2 - t) * ldcp, 1, 3 * ldcp},
+         MatView{p->Z, 1, p->rcap}, 0.0, p->T1 + (size_t)(m + t) * ldcp, 1, 3 * ldcp, p->ws, p->ws_elems, st);
   gemm(kr, p->nQR, nc, 1.0, MatView{p->T1, 1, ldcp}, MatView{p->CRm, p->ldcr, 1}, 0.0, p->T2, 1, ldcp, p->ws,
        p->ws_elems, st);
   mat_dot(kr, p->nQR, p->T2, ldcp, p->T2, ldcp, p->ds + DS_RN, st);
@@ -2128,7 +2136,6 @@ cr_status cr_create(const cr_problem_desc* d_in, const cr_options* o, cr_problem
   CK(dalloc(p, &p->Ep, (size_t)ny * m));
   CK(dalloc(p, &p->CE, (size_t)m * m));
   CK(dalloc(p, &p->CP, (size_t)p->ldcp * p->ldm));
-  CK(dalloc(p, &p->Mc, (size_t)p->ldm * p->ldm));
   CK(dalloc(p, &p->T1, (size_t)p->ldcp * p->ldm));
   CK(dalloc(p, &p->T2, (size_t)p->ldcp * p->ldm));
   CK(dalloc(p, &p->gram, (size_t)m * m));

@@ -74,36 +74,77 @@ __global__ void gemm_reduce_kernel(int M, int N, int S, const double* __restrict
 }
 
 // one warp per output column p
-__global__ void gemv_t_kernel(int n, int k, const double* __restrict__ A, int64_t lda, const double* __restrict__ w,
-                              double* out, int64_t ostride, double alpha, double beta) {
-  const int lane = threadIdx.x & 31;
-  const int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+// out[p] = alpha * A(:, p)^T w (+ beta out[p]): one CTA of 256 threads per column,
+// four independent accumulators per thread (rows strided by 256, so loads of
+// consecutive threads coalesce and four are in flight), then a fixed-order
+// reduction over the CTA (warp shuffles, then the eight warp sums in order).
+constexpr int kGvThreads = 256;
+
+__global__ void __launch_bounds__(kGvThreads) gemv_t_kernel(int n, int k, const double* __restrict__ A, int64_t lda,
+                                                            const double* __restrict__ w, double* out,
+                                                            int64_t ostride, double alpha, double beta) {
+  const int p = blockIdx.x;
   if (p >= k) return;
   const double* a = A + (int64_t)p * lda;
-  double acc0 = 0.0, acc1 = 0.0;
-  int i = lane;
-  for (; i + 32 < n; i += 64) {
-    acc0 = fma(a[i], w[i], acc0);
-    acc1 = fma(a[i + 32], w[i + 32], acc1);
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  int i = threadIdx.x;
+  for (; i + 3 * kGvThreads < n; i += 4 * kGvThreads) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] = fma(a[i + u * kGvThreads], w[i + u * kGvThreads], acc[u]);
   }
-  if (i < n) acc0 = fma(a[i], w[i], acc0);
-  double acc = warp_sum(acc0 + acc1);
-  if (lane == 0) {
+#pragma unroll
+  for (int u = 0; u < 3; ++u) {
+    const int ii = i + u * kGvThreads;
+    if (ii < n) acc[u] = fma(a[ii], w[ii], acc[u]);
+  }
+  double v = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+  v = warp_sum(v);
+  __shared__ double red[kGvThreads / 32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < kGvThreads / 32; ++q) t += red[q];
     double* o = out + (int64_t)p * ostride;
-    *o = beta == 0.0 ? alpha * acc : fma(alpha, acc, beta * *o);
+    *o = beta == 0.0 ? alpha * t : fma(alpha, t, beta * *o);
   }
 }
 
-__global__ void gemv_n_kernel(int n, int k, const double* __restrict__ A, int64_t lda, const double* __restrict__ c,
-                              int64_t cs, double* y, double alpha, double beta) {
+// y[i] = alpha * sum_p A(i, p) c[p] (+ beta y[i]): a CTA takes 32 consecutive rows;
+// its eight warps split the columns in eight fixed ranges (lane = row, so loads
+// coalesce), four accumulators per thread, and the eight partial sums of a row
+// are added in order.
+__global__ void __launch_bounds__(kGvThreads) gemv_n_kernel(int n, int k, const double* __restrict__ A, int64_t lda,
+                                                            const double* __restrict__ c, int64_t cs, double* y,
+                                                            double alpha, double beta) {
   extern __shared__ double cs_sm[];
   for (int p = threadIdx.x; p < k; p += blockDim.x) cs_sm[p] = c[(int64_t)p * cs];
   __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double acc = 0.0;
-  for (int p = 0; p < k; ++p) acc = fma(A[i + (int64_t)p * lda], cs_sm[p], acc);
-  y[i] = beta == 0.0 ? alpha * acc : fma(alpha, acc, beta * y[i]);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
+  const int kc = (k + 7) / 8, p0 = min(k, wid * kc), p1 = min(k, p0 + kc);
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  if (i < n) {
+    const double* a = A + i;
+    int p = p0;
+    for (; p + 3 < p1; p += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] = fma(a[(int64_t)(p + u) * lda], cs_sm[p + u], acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+      if (p + u < p1) acc[u] = fma(a[(int64_t)(p + u) * lda], cs_sm[p + u], acc[u]);
+  }
+  __shared__ double part[8][33];
+  part[wid][lane] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+  __syncthreads();
+  if (wid == 0 && i < n) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t += part[q][lane];
+    y[i] = beta == 0.0 ? alpha * t : fma(alpha, t, beta * y[i]);
+  }
 }
 
 __global__ void dot_kernel(int n, const double* __restrict__ x, const double* __restrict__ y, double* out) {
@@ -143,16 +184,38 @@ __global__ void spmv_x_kernel(int n, const int* __restrict__ rp, const int* __re
   y[i] = beta == 0.0 ? alpha * acc : fma(alpha, acc, beta * y[i]);
 }
 
-__global__ void omega_sq_kernel(int n, int m, const uint8_t* __restrict__ Om, int64_t ldo,
-                                const double* __restrict__ u, double* out) {
-  const int lane = threadIdx.x & 31;
-  const int a = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+// out[a] = sum_i Om(i, a) u_i^2: one CTA per injection, laid out as gemv_t_kernel.
+__global__ void __launch_bounds__(kGvThreads) omega_sq_kernel(int n, int m, const uint8_t* __restrict__ Om,
+                                                              int64_t ldo, const double* __restrict__ u,
+                                                              double* out) {
+  const int a = blockIdx.x;
   if (a >= m) return;
   const uint8_t* o = Om + (int64_t)a * ldo;
-  double acc = 0.0;
-  for (int i = lane; i < n; i += 32) acc = fma((double)o[i] * u[i], u[i], acc);
-  acc = warp_sum(acc);
-  if (lane == 0) out[a] = acc;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  int i = threadIdx.x;
+  for (; i + 3 * kGvThreads < n; i += 4 * kGvThreads) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const double x = u[i + q * kGvThreads];
+      acc[q] = fma((double)o[i + q * kGvThreads] * x, x, acc[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int ii = i + q * kGvThreads;
+    if (ii < n) acc[q] = fma((double)o[ii] * u[ii], u[ii], acc[q]);
+  }
+  double v = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+  v = warp_sum(v);
+  __shared__ double red[kGvThreads / 32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < kGvThreads / 32; ++q) t += red[q];
+    out[a] = t;
+  }
 }
 
 __global__ void scale_inv_norm_kernel(int n, const double* __restrict__ x, const double* nrm2, double* y) {
@@ -226,9 +289,8 @@ void gemm(int M, int N, int K, double alpha, MatView A, MatView B, double beta, 
 void gemv_t(int n, int k, const double* A, int64_t lda, const double* w, double* out, int64_t ostride,
             double alpha, double beta, cudaStream_t st) {
   if (k <= 0) return;
-  const int wpb = 8;
   count_launch();
-  gemv_t_kernel<<<(k + wpb - 1) / wpb, 32 * wpb, 0, st>>>(n, k, A, lda, w, out, ostride, alpha, beta);
+  gemv_t_kernel<<<k, kGvThreads, 0, st>>>(n, k, A, lda, w, out, ostride, alpha, beta);
 }
 
 void gemv_n(int n, int k, const double* A, int64_t lda, const double* c, int64_t cstride, double* y, double alpha,
@@ -237,11 +299,11 @@ void gemv_n(int n, int k, const double* A, int64_t lda, const double* c, int64_t
   if (k <= 0) {
     if (beta == 1.0) return;
     count_launch();
-    gemv_n_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, 0, A, lda, c, cstride, y, alpha, beta);
+    gemv_n_kernel<<<(n + 31) / 32, kGvThreads, 0, st>>>(n, 0, A, lda, c, cstride, y, alpha, beta);
     return;
   }
   count_launch();
-  gemv_n_kernel<<<(n + 255) / 256, 256, sizeof(double) * k, st>>>(n, k, A, lda, c, cstride, y, alpha, beta);
+  gemv_n_kernel<<<(n + 31) / 32, kGvThreads, sizeof(double) * k, st>>>(n, k, A, lda, c, cstride, y, alpha, beta);
 }
 
 void dot(int n, const double* x, const double* y, double* out, cudaStream_t st) {
@@ -266,7 +328,7 @@ void spmv_x(int n, const int* rowptr, const int* col, const double* val, const d
 void omega_sq_dots(int n, int m, const uint8_t* Om, int64_t ldo, const double* u, double* out, cudaStream_t st) {
   if (m <= 0) return;
   count_launch();
-  omega_sq_kernel<<<(m + 7) / 8, 256, 0, st>>>(n, m, Om, ldo, u, out);
+  omega_sq_kernel<<<m, kGvThreads, 0, st>>>(n, m, Om, ldo, u, out);
 }
 
 void scale_by_inv_norm(int n, const double* x, const double* nrm2, double* y, cudaStream_t st) {

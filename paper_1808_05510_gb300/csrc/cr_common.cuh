@@ -389,10 +389,6 @@ void copy2d(int r, int c, const double* src, int64_t lds, double* dst, int64_t l
 void cg_update_zr(int j, double* Z, double* R, const double* P, const double* Q, int64_t ld, const double* gs, int k,
                   cudaStream_t st);
 void cg_update_p(int j, double* P, const double* R, int64_t ld, const double* gs, int k, cudaStream_t st);
-// Core of the residual norm: M (n x n, n = m + 3j): identity on the first m
-// columns, and for the factor block (3p+s, 3q+t): -lam Z(p,q) for (s,t)=(0,2),
-// -2 lam Z(p,q) for (1,1), -lam Z(p,q) for (2,0).
-void build_core(int m, int j, const double* Z, int64_t ldz, double lam, double* Mc, int64_t ldm, cudaStream_t st);
 // Dg(p, q) = diagonal of the projected operator at Z(p, q) (Jacobi preconditioner of the Galerkin CG)
 void galerkin_diag(int j, int m, const double* A1, const double* A2, const double* B1, const double* B2,
                    const double* G, const double* H, int64_t ld, double lam, double* Dg, cudaStream_t st);

@@ -154,22 +154,6 @@ __global__ void cg_p_kernel(int j, double* P, const double* __restrict__ R, int6
   P[o] = fma(beta, P[o], R[o]);
 }
 
-__global__ void build_core_kernel(int m, int j, const double* __restrict__ Z, int64_t ldz, double lam, double* Mc,
-                                  int64_t ldm) {
-  const int n = m + 3 * j;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)n * n) return;
-  const int a = (int)(t % n), b = (int)(t / n);
-  double v = 0.0;
-  if (a < m || b < m) {
-    v = (a == b) ? 1.0 : 0.0;
-  } else {
-    const int pa = (a - m) / 3, sa = (a - m) % 3, qb = (b - m) / 3, tb = (b - m) % 3;
-    if (sa + tb == 2) v = (sa == 1 ? -2.0 : -1.0) * lam * Z[pa + (int64_t)qb * ldz];
-  }
-  Mc[a + (int64_t)b * ldm] = v;
-}
-
 inline unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b); }
 
 }  // namespace
@@ -244,12 +228,6 @@ void cg_update_zr(int j, double* Z, double* R, const double* P, const double* Q,
 void cg_update_p(int j, double* P, const double* R, int64_t ld, const double* gs, int k, cudaStream_t st) {
   count_launch();
   cg_p_kernel<<<nblk((int64_t)j * j), 256, 0, st>>>(j, P, R, ld, gs, k);
-}
-
-void build_core(int m, int j, const double* Z, int64_t ldz, double lam, double* Mc, int64_t ldm, cudaStream_t st) {
-  const int64_t n = m + 3 * (int64_t)j;
-  count_launch();
-  build_core_kernel<<<nblk(n * n), 256, 0, st>>>(m, j, Z, ldz, lam, Mc, ldm);
 }
 
 }  // namespace cr
