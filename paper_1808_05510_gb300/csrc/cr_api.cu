@@ -1346,6 +1346,9 @@ void eig_operator(cr_problem* p) {
 // Relative Galerkin residual that counts as "to rounding": smaller targets (tau = 0)
 // are raised to it, so that a CG whose residual has reached the rounding floor stops.
 constexpr double kGalTolFloor = 1e-14;
+// Mixed form: each float32 inner solve of the Galerkin refinement stops at
+// |r|^2 <= kGalInner |R|^2 (R the float64 residual of the outer step).
+constexpr double kGalInner = 1e-7;
 
 cr_status do_project(cr_problem* p, double tol, cr_proj_info* info) {
   tol = std::max(tol, kGalTolFloor);
@@ -1439,12 +1442,12 @@ cr_status do_project(cr_problem* p, double tol, cr_proj_info* info) {
       cudaError_t ce = cudaErrorNotSupported;
       if (!(eig && p->smw_ok))
         ce = galerkin_cluster_f32_launch(j, p->m, ld, p->lam, p->fA1, p->fA2, p->fB1, p->fB2, p->fG, p->fH, p->fF,
-                                         p->fDg, p->fZ, 1e-7 * rr, inner_maxit, p->gout, st, eig ? &fe : nullptr);
+                                         p->fDg, p->fZ, kGalInner * rr, inner_maxit, p->gout, st, eig ? &fe : nullptr);
       if (ce == cudaErrorNotSupported) {
         cudaGetLastError();
         ce = galerkin_cg_launch<float>(p->gal_nb, j, p->m, ld, p->lam, p->fA1, p->fA2, p->fB1, p->fB2, p->fG, p->fH,
                                        p->fF, p->fDg, p->fZ, p->fR, p->fPa, p->fPb, p->fQ, p->fT2, p->fT1, p->fTH,
-                                       p->fGw, p->fzb, p->gpart, p->gbar, p->gerr, 1e-7 * rr, inner_maxit, p->gout,
+                                       p->fGw, p->fzb, p->gpart, p->gbar, p->gerr, kGalInner * rr, inner_maxit, p->gout,
                                        st, eig ? &fe : nullptr);
       }
       CUCHK(p, ce);
