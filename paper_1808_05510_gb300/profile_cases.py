@@ -9,6 +9,9 @@
     python -m paper_1808_05510_gb300.profile_cases galerkin fp64|mixed [eigen|jacobi]
         two Galerkin projections (Eq. Proj_Sylv) at rank 60 from a float64 greedy run,
         in the eigenbasis form (default) or the original-basis Jacobi form
+    python -m paper_1808_05510_gb300.profile_cases galerkin_scan fp64|mixed
+        one projection at each of j = 60, 100, 250, 500 in both forms (CUDA-event
+        phase times): iterations and time per CG iteration
     python -m paper_1808_05510_gb300.profile_cases assembly tc
         three tensor-core assemblies of G_a = U^T diag(Omega_a) U at rank 100
     python -m paper_1808_05510_gb300.profile_cases post fp64
@@ -72,6 +75,45 @@ def galerkin(form: str, gform: str = "eigen") -> None:
         for k in range(2):
             g.cr_set_factors(U, Z * (1.0 + 1e-3 * (k + 1)), V)
             print(g.cr_project(5e-10), flush=True)
+
+
+def galerkin_scan(form: str) -> None:
+    """Galerkin projections at j = 60, 100, 250, 500 on the visual-cortex workload
+    from orthonormal smoothed-noise factors and a small Z, to relative residual
+    5e-10, in both forms: CG iterations, the Galerkin phase's device time (CUDA
+    events, profile mode) without the eigenbasis build, and the time per iteration."""
+    import json
+
+    import scipy.sparse as sp
+
+    from . import synth
+    from .conreg import CR_FP64, CR_GALERKIN_EIGEN, CR_GALERKIN_JACOBI, CR_MIXED, ConReg
+
+    p = synth.visual_cortex()
+    rng = np.random.default_rng(7)
+
+    def basis(L, j):
+        A = sp.csr_matrix((L.val, L.col, L.rowptr), shape=(L.n, L.n))
+        W = rng.standard_normal((L.n, j))
+        d = A.diagonal().max()
+        for _ in range(3):
+            W = W - (A @ W) / (2 * d)
+        return np.linalg.qr(W)[0]
+
+    prec = CR_MIXED if form == "mixed" else CR_FP64
+    for j in (60, 100, 250, 500):
+        U, V = basis(p.Ly, j), basis(p.Lx, j)
+        Z = 1e-3 * rng.standard_normal((j, j))
+        for name, gf in (("eigen", CR_GALERKIN_EIGEN), ("jacobi", CR_GALERKIN_JACOBI)):
+            with ConReg.from_problem(p, r_cap=j, precision=prec, galerkin_form=gf, profile=1) as g:
+                g.cr_set_factors(U, Z, V)
+                g.cr_get_stats(reset=True)
+                info = g.cr_project(5e-10)
+                st = g.cr_get_stats()
+            ms = st["phase_ms"]["galerkin"] - st["phase_ms"]["basis"]
+            print(json.dumps({"j": j, "form": name, "precision": form, "iters": info["iters"],
+                              "galerkin_ms": round(ms, 3), "basis_ms": round(st["phase_ms"]["basis"], 3),
+                              "us_per_iter": round(1e3 * ms / max(info["iters"], 1), 2)}), flush=True)
 
 
 def assembly(form: str) -> None:
@@ -150,4 +192,5 @@ if __name__ == "__main__":
         pcg_stress(form, int(sys.argv[3]) if len(sys.argv) > 3 else 2)
     else:
         extra = sys.argv[3:4]
-        {"pcg": pcg, "galerkin": galerkin, "assembly": assembly, "post": post}[case](form, *extra)
+        {"pcg": pcg, "galerkin": galerkin, "galerkin_scan": galerkin_scan, "assembly": assembly,
+         "post": post}[case](form, *extra)
