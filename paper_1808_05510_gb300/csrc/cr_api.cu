@@ -258,6 +258,7 @@ struct cr_problem {
   double *QL = nullptr, *CL = nullptr, *QR = nullptr, *CRm = nullptr, *Cx = nullptr, *Cx2 = nullptr, *Ep = nullptr,
          *CE = nullptr, *CP = nullptr, *T1 = nullptr, *T2 = nullptr, *gram = nullptr, *tmat = nullptr;
   int nQL = 0, nQR = 0, nQX = 0;
+  std::vector<int> qr_step;  // greedy step that created right-basis vector nQX + i
   int64_t ldcl = 0, ldcr = 0, ldcx = 0, ldcp = 0, ldm = 0;
   double* ws = nullptr;
   size_t ws_elems = 0;
@@ -1184,7 +1185,10 @@ cr_status grow_bases(cr_problem* p, int q) {
     copy(p->nx, col, dst, st);
     double ratio = 0.0;
     TRY(cgs2(p, p->nx, p->QR, p->nx, p->nQR, dst, &ratio));
-    if (ratio > 1e-12) ++p->nQR;
+    if (ratio > 1e-12) {
+      ++p->nQR;
+      p->qr_step.push_back(q);
+    }
   }
   for (int s = 0; s < 3; ++s)
     gemv_t(p->nx, p->nQR, p->QR, p->nx, p->VV + (size_t)(3 * q + s) * p->nx,
@@ -1686,8 +1690,17 @@ cr_status do_relres(cr_problem* p, double* relres) {
   for (int t = 0; t < 3; ++t)
     gemm(kr, j, j, -p->lam * (t == 1 ? 2.0 : 1.0), MatView{p->CP + (size_t)(m + 2 - t) * ldcp, 1, 3 * ldcp},
          MatView{p->Z, 1, p->rcap}, 0.0, p->T1 + (size_t)(m + t) * ldcp, 1, 3 * ldcp, p->ws, p->ws_elems, st);
-  gemm(kr, p->nQR, nc, 1.0, MatView{p->T1, 1, ldcp}, MatView{p->CRm, p->ldcr, 1}, 0.0, p->T2, 1, ldcp, p->ws,
-       p->ws_elems, st);
+  // T2 = T1 C_Q^T.  C_Q is block upper triangular: right-basis vector r created in
+  // greedy step q_r has coefficients only on the data columns (r < nQX) or the panel
+  // columns of steps >= q_r, so each 64-column block of T2 sums from column
+  // m + 3 q_r0 on.
+  for (int r0 = 0; r0 < p->nQR; r0 += 64) {
+    const int r1 = std::min(p->nQR, r0 + 64);
+    const int k0 = r0 < p->nQX ? 0 : m + 3 * p->qr_step[r0 - p->nQX];
+    gemm(kr, r1 - r0, nc - k0, 1.0, MatView{p->T1 + (size_t)k0 * ldcp, 1, ldcp},
+         MatView{p->CRm + r0 + (size_t)k0 * p->ldcr, p->ldcr, 1}, 0.0, p->T2 + (size_t)r0 * ldcp, 1, ldcp, p->ws,
+         p->ws_elems, st);
+  }
   mat_dot(kr, p->nQR, p->T2, ldcp, p->T2, ldcp, p->ds + DS_RN, st);
   TRY(readback(p, DS_RN, 1, false));
   *relres = p->Dnorm > 0.0 ? std::sqrt(p->hs->ds[DS_RN]) / p->Dnorm : 0.0;
@@ -2530,6 +2543,7 @@ cr_status cr_set_factors(cr_problem* p, int32_t j, const double* U, int64_t ldu,
   fill((int64_t)p->ldcr * p->ldcr - (int64_t)p->ldcr * p->m, 0.0, p->CRm + (size_t)p->ldcr * p->m, st);
   p->nQL = 0;
   p->nQR = p->nQX;  // the X part of the right basis does not depend on the factors
+  p->qr_step.clear();
   p->j = 0;
   eig_reset(p);
   if (j > 0) {
