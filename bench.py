@@ -67,10 +67,13 @@ def parse(argv=None):
                     help="preconditioner of the ALS sub-solves in the headline forms")
     ap.add_argument("--no-jacobi", action="store_true", help="skip the Jacobi-PCG forms timed beside the headline")
     ap.add_argument("--ttr-r", type=int, default=500, help="rank cap of the visual-cortex time to relres 1e-6")
+    ap.add_argument("--ttr-resid-every", type=int, default=0,
+                    help="visual-cortex time to relres: evaluate relres every k greedy steps, 0 = the library's "
+                         "automatic schedule (dW every step)")
     ap.add_argument("--no-cortex", action="store_true", help="skip the whole-cortex line")
     ap.add_argument("--cortex-r", type=int, default=300, help="rank cap of the whole-cortex line")
-    ap.add_argument("--cortex-resid-every", type=int, default=10,
-                    help="whole-cortex: evaluate relres every k greedy steps (dW every step)")
+    ap.add_argument("--cortex-resid-every", type=int, default=0,
+                    help="whole-cortex: evaluate relres every k greedy steps, 0 = automatic (dW every step)")
     return ap.parse_args(argv)
 
 
@@ -360,7 +363,7 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_batch:
         forms["batched"] = measure_batch(args, rank, world, dev, precond=head_pc)
     ttr_toy = None if args.no_ttr else measure_ttr_toy(args)
-    ttr_visual = None if args.no_ttr else measure_ttr(p, args, head_pc, r_cap=args.ttr_r,
+    ttr_visual = None if args.no_ttr else measure_ttr(p, args, head_pc, r_cap=args.ttr_r, resid_every=args.ttr_resid_every,
                                                       label="visual-cortex workload (7,530 voxels, 28 injections, "
                                                             "lambda 100)")
     cortex = None if args.no_cortex else measure_cortex(args, head_pc)

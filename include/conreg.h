@@ -146,7 +146,9 @@ typedef struct {
   int32_t als_max_iter;    /* cap on ALS sweeps (default 10) */
   int32_t als_sweeps;      /* > 0: run exactly this many sweeps (deterministic comparisons) */
   int32_t galerkin_maxit;  /* cap on Galerkin CG iterations per projection (default 10 j^2 + 100) */
-  int32_t residual_every;  /* cr_solve: evaluate ‖R‖_F every k steps (default 1) */
+  int32_t residual_every;  /* cr_solve: evaluate ‖R‖_F every k steps (default 1); 0 = automatic: after each
+                              check, at half the steps that relres's observed decay predicts to the target
+                              (1 to 32), so sparse far from it and every step close to it */
   int32_t cluster_size;    /* PCG thread-block cluster size; 0 = automatic */
   int32_t profile;         /* != 0: time each phase with CUDA events (see cr_get_stats) */
   int32_t pcg_kernel;      /* 0 = automatic: the register-resident cluster kernel (the whole solve on

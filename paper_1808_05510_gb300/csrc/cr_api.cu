@@ -2369,6 +2369,13 @@ cr_status cr_solve(cr_problem* p, int32_t r_max, double tau, double relres_targe
   si.dW = NAN;
   cr_status rc = CR_OK;
   int step = 0;
+  // residual_every == 0: the checks follow relres's observed decay.  After a check
+  // the rate per step from the previous one predicts the steps left to the target;
+  // the next check comes after half of them (1 to kMaxGap steps), so checks are
+  // sparse far from the target and every step close to it.
+  constexpr int kMaxGap = 32;
+  int next_check = 1, last_step = 0;
+  double last_rr = 0.0;
   while (p->j < std::min(r_max, p->rcap)) {
     cr_rank1_info ri{};
     cr_status s = do_rank_one(p, &ri);
@@ -2388,10 +2395,23 @@ cr_status cr_solve(cr_problem* p, int32_t r_max, double tau, double relres_targe
     double dW = 0.0;
     double* rr = nullptr;
     double relres = NAN;
-    if (relres_target > 0.0 && (step % std::max(1, p->opt.residual_every) == 0 || p->j >= r_max)) rr = &relres;
+    const bool due = p->opt.residual_every == 0 ? step >= next_check
+                                                : step % std::max(1, p->opt.residual_every) == 0;
+    if (relres_target > 0.0 && (due || p->j >= r_max)) rr = &relres;
     TRY(cr_residual(p, rr, nullptr, &dW));
     si.dW = dW;
-    if (rr) si.relres = relres;
+    if (rr) {
+      si.relres = relres;
+      int gap = 1;
+      if (last_rr > 0.0 && relres > relres_target && relres < last_rr && step > last_step) {
+        const double rate = std::log(last_rr / relres) / (step - last_step);
+        const double left = std::log(relres / relres_target) / rate;
+        gap = (int)std::max(1.0, std::min((double)kMaxGap, std::floor(0.5 * left)));
+      }
+      next_check = step + gap;
+      last_rr = relres;
+      last_step = step;
+    }
     if (dW <= tau) {
       si.stop = CR_STOP_DW;
       break;
